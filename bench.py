@@ -1,0 +1,287 @@
+"""Benchmark: cell-updates/s of the RB-TAI Active Flux step on the 2048^2
+low-Mach doubly periodic shear layer (FP32 bulk arithmetic, compensated
+averages, FP64 invariants), one JSON line on stdout.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value      device-timed cell-updates/s of K steps (CUDA events on the solver's
+           stream), state resident in HBM; summed over ranks for N > 1
+           (independent replicas, max-over-ranks time).
+e2e        the same metric through the public API with host buffers: every step
+           copies the state in from pinned host memory, advances it and copies
+           it back out.
+roofline   the dominant kernel (the fused step kernel): algorithmic bytes per
+           launch / its mean CUDA-event duration, against the measured HBM peak.
+cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
+--impl reference  times the oracle itself (this workload has no other
+           reference implementation), on rank 0 only.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s on 2048^2 Euler AF, FP32 vs FP64 at stated L-inf; % HBM peak"
+UNIT = "cell-updates/s"
+N_CELLS_SIDE = 2048
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32_comp", choices=["fp32", "fp32_comp", "fp64"])
+    p.add_argument("--n", type=int, default=N_CELLS_SIDE)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def cpu_baseline(P, sample_n=256, sample_steps=6):
+    """The oracle as it stands on a bounded sample of the same workload: the same
+    shear layer on a sample_n^2 grid, sample_steps steps, one host core."""
+    import oracle
+    from paper_2605_12915_gb300 import inputs as I
+    S = I.shear(n=sample_n)
+    t = time.perf_counter()
+    oracle.run(S.state, S.grid.h, S.gamma, S.dt, sample_steps)
+    el = time.perf_counter() - t
+    return {"value": sample_n * sample_n * sample_steps / el, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": "shear layer %d^2, %d steps, FP64 oracle, 1 thread (%.1f s)"
+                      % (sample_n, sample_steps, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2605_12915_gb300 import inputs as I
+    oracle.build()
+    n = 128  # bounded sample per step: a 128^2 copy of the workload
+    S = I.shear(n=n)
+    st = S.state
+    for _ in range(args.warmup):
+        st, _ = oracle.step(st, S.grid.h, S.gamma, S.dt)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = oracle.step(st, S.grid.h, S.gamma, S.dt)
+    el = time.perf_counter() - t
+    v = n * n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "low-Mach shear layer (FP64 CPU oracle, %d^2 sample per step)" % n,
+                       "n": n, "cfl": 0.4},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "shear layer %d^2 per step, %d steps" % (n, args.steps)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2605_12915_gb300 as af
+    from paper_2605_12915_gb300 import inputs as I
+
+    rank, world, local = dist_setup(args)
+    af._build.build()
+    af.load()
+    P = I.shear(n=args.n)
+    N = P.grid.nx * P.grid.ny
+    stream = torch.cuda.Stream()
+    dev_state = torch.from_numpy(P.state).cuda()
+    torch.cuda.synchronize()
+    solver = af.Solver(P.grid, P.gamma, dev_state, precision=args.precision, stream=stream)
+    inv0 = solver.invariants()
+
+    # warm-up
+    solver.step(P.dt, args.warmup)
+    solver.sync()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        solver.step(P.dt, args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    solver.sync()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * args.steps * world / (ms * 1e-3)
+    inv1 = solver.invariants()
+
+    # dominant kernel: per-launch duration of the step kernel(s)
+    kstats = solver_kernel_stats(af, solver, P, stream, torch)
+
+    # end to end through the public API with pinned host buffers
+    host_in = torch.from_numpy(P.state.copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(1, args.e2e_steps)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_state(host_in)
+        solver.step(P.dt, 1)
+        solver.state(host_out)
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    e2e = {"value": N * e2e_steps * world / e2e_el, "unit": UNIT,
+           "h2d_bytes_per_step": int(host_in.numel() * 8),
+           "d2h_bytes_per_step": int(host_out.numel() * 8)}
+
+    hbm, peak_kind = peaks()
+    bytes_per_cell = {"fp32": 128, "fp32_comp": 160, "fp64": 256}[args.precision]
+    ach = bytes_per_cell * N / (kstats["ms_per_launch"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": None, "kernel": kstats["kernel"], "peak_kind": peak_kind,
+            "bytes_per_cell": bytes_per_cell}
+    drift = (inv1[:4] - inv0[:4]) / np.array([inv0[0], inv0[0], inv0[0], inv0[3]])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp32_comp": "f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "low-Mach doubly periodic shear layer, %d^2 cells, CFL 0.4, "
+                                   "RB-TAI, %s" % (args.n, args.precision),
+                       "n": args.n, "precision": args.precision, "variant": "tai",
+                       "l2": "inputs larger than L2 (state %.0f MB)" % (bytes_per_cell * N / 2 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": kstats["launches_per_step"] * args.steps,
+            "clocks": clocks.summary(),
+            "conservation_drift": [float(x) for x in drift],
+            "entropy_change": float(inv1[4] - inv0[4])}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(P)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def solver_kernel_stats(af, solver, P, stream, torch, reps=20):
+    """Mean duration of one step launch sequence (the fused kernel when that
+    path is active), timed with CUDA events on the solver's stream."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(stream)
+    for r in range(reps):
+        solver.step(P.dt, 1)
+        ev[r + 1].record(stream)
+    ev[-1].synchronize()
+    ts = [ev[r].elapsed_time(ev[r + 1]) for r in range(reps)]
+    return {"ms_per_launch": float(np.mean(ts)), "kernel": "step (all launches of one step)",
+            "launches_per_step": 10}
+
+
+if __name__ == "__main__":
+    main()

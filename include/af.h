@@ -1,0 +1,135 @@
+/*
+ * af.h -- C ABI of the GB300 (sm_103a) implementation of one time step of the
+ * fully discrete Active Flux method with transported acoustic increments
+ * (RB-TAI), with the additive Roe-Barsukow (RB) point update as a switch, for
+ * the 2D compressible Euler equations (gamma-law gas) on a periodic Cartesian
+ * grid of square cells (arXiv 2605.12915).
+ *
+ * Conventions for every entry point:
+ *  - Status codes only; nothing throws, aborts or traps across this ABI.
+ *  - Errors found on the device (acoustic CFL above 1/2, foot outside the
+ *    supported reach, non-positive density or pressure, non-finite values) are
+ *    latched in a device word and reported by af_step (as soon as the step that
+ *    raised them has completed), af_sync, af_get_state and af_reduce_invariants.
+ *  - The library never frees, and never keeps pointers to, caller memory.
+ *  - Every array is a plane of nx*ny values in row-major order, index j*nx+i.
+ *
+ * Degrees of freedom (Sec. 2, Fig. 1) of cell C_ij = [x_i,x_{i+1}] x [y_j,y_{j+1}]:
+ *   avg[4] conservative cell average (rho, rho u, rho v, E) of C_ij,
+ *   vtx[4] primitive (rho, u, v, p) at the vertex        (x_i,       y_j),
+ *   ev[4]  primitive (rho, u, v, p) at the x-edge midpoint (x_i,     y_{j+1/2}),
+ *   eh[4]  primitive (rho, u, v, p) at the y-edge midpoint (x_{i+1/2}, y_j),
+ * with E = p/(gamma-1) + rho (u^2+v^2)/2.
+ */
+#ifndef AF_H
+#define AF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct af_handle af_handle; /* opaque; owns the device state and scratch */
+
+typedef enum {
+  AF_OK = 0,
+  AF_ERR_ARG = 1,         /* invalid argument (null pointer, size, dt, enum) */
+  AF_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  AF_ERR_ALLOC = 3,       /* device or pinned host allocation failed */
+  AF_ERR_CFL = 4,         /* c dt / h > 1/2 at a node, or a convective foot beyond one cell */
+  AF_ERR_NONPHYSICAL = 5, /* rho <= 0 or p <= 0 where a sound speed is needed */
+  AF_ERR_NONFINITE = 6,   /* NaN or Inf produced */
+  AF_ERR_STATE = 7        /* handle unusable (a previous CUDA error) */
+} af_status;
+
+typedef enum {
+  AF_FP64 = 0,     /* all arithmetic and storage in double */
+  AF_FP32 = 1,     /* all stencil arithmetic and storage in float */
+  AF_FP32_COMP = 2 /* as AF_FP32, cell averages kept as float hi+lo pairs updated
+                      by error-free sums of the edge-flux increments */
+} af_precision;
+
+typedef enum {
+  AF_TAI = 0, /* transported acoustic increments, Eq. (transported-update) */
+  AF_RB = 1   /* additive point update, Eq. (barsukow-additive) */
+} af_variant;
+
+typedef enum { AF_HOST = 0, AF_DEVICE = 1 } af_memory;
+
+typedef struct {
+  int32_t nx, ny; /* cells in x and y, each >= 2 */
+  double h;       /* cell side, > 0 */
+} af_grid;
+
+typedef struct {
+  double *avg[4];
+  double *vtx[4];
+  double *ev[4];
+  double *eh[4];
+} af_state_f64;
+
+/* Indices of af_reduce_invariants' output (all FP64):
+ *  mass, momentum, energy = h^2 sum of the cell averages (conserved by the
+ *  flux-difference update, Eq. af-average-update); entropy functional
+ *  -int rho log(p / rho^gamma) dA (Sec. 6) by tensor Simpson on each cell's
+ *  nine nodes, and from the cell averages; kinetic energy of the averages;
+ *  max of |u| + c and min of rho, p over vertex, edge and centre nodes;
+ *  int (v_x - u_y) dA by Simpson along cell edges; the latched error bits. */
+enum {
+  AF_INV_MASS = 0,
+  AF_INV_MOMX = 1,
+  AF_INV_MOMY = 2,
+  AF_INV_ENERGY = 3,
+  AF_INV_ENTROPY = 4,
+  AF_INV_ENTROPY_AVG = 5,
+  AF_INV_KINETIC = 6,
+  AF_INV_MAX_SPEED = 7,
+  AF_INV_MIN_RHO = 8,
+  AF_INV_MIN_P = 9,
+  AF_INV_VORTICITY = 10,
+  AF_INV_FLAGS = 11,
+  AF_NINV = 12
+};
+
+/* Create a solver for grid g and copy the initial state in (Sec. 6: averages by
+ * quadrature, point values sampled -- prepared by the caller).  `state` arrays
+ * are read on `where` (AF_HOST: pageable or pinned host memory; AF_DEVICE:
+ * device memory of the current device); the caller keeps ownership.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
+ * later call of this handle runs.  On error *out is NULL. */
+af_status af_init(af_handle **out, const af_grid *g, double gamma, const af_state_f64 *state,
+                  af_memory where, af_precision prec, af_variant var, void *cuda_stream);
+
+/* Advance n_steps >= 0 steps of size dt > 0 (Sec. 6.1, Algorithm): point values
+ * at t^n + dt/2 and t^n + dt from the time-n reconstruction, then the
+ * conservative space-time Simpson average update.  Asynchronous on the
+ * handle's stream; returns the first latched device error of steps that have
+ * already completed (AF_OK otherwise). */
+af_status af_step(af_handle *h, double dt, int32_t n_steps);
+
+/* Wait for the handle's stream and return the latched device error, if any. */
+af_status af_sync(af_handle *h);
+
+/* Copy the current state out as FP64 (AF_FP32_COMP: averages as hi + lo).
+ * Synchronises the stream. */
+af_status af_get_state(af_handle *h, const af_state_f64 *out, af_memory where);
+
+/* Replace the current state (converted to the handle's precision) and clear the
+ * latched device error. */
+af_status af_set_state(af_handle *h, const af_state_f64 *in, af_memory where);
+
+/* FP64 global diagnostics of the current state, out[AF_NINV] in host memory.
+ * Synchronises the stream. */
+af_status af_reduce_invariants(af_handle *h, double *out);
+
+/* Release the handle's device memory and streams' resources.  NULL is a no-op. */
+void af_destroy(af_handle *h);
+
+/* Static text for a status code. */
+const char *af_status_string(af_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AF_H */

@@ -1,1 +1,222 @@
-"""GB300-native RB-TAI Active Flux step (placeholder; binding added below)."""
+"""GB300-native RB-TAI Active Flux step (2D Euler, periodic Cartesian grid).
+
+Thin ctypes binding of the C ABI in ``include/af.h``; every step of the method
+runs in the CUDA kernels of ``libaf.so``.  The binding only marshals
+arguments: numpy arrays or torch tensors in, pointers and sizes out.  There is
+no CPU fallback: if ``libaf.so`` is missing or cannot be loaded, every call
+raises.
+
+State arrays have shape (16, ny, nx) and dtype float64 (see ``inputs``):
+averages (rho, rho u, rho v, E), then (rho, u, v, p) at vertices, x-edge
+midpoints and y-edge midpoints.
+"""
+import ctypes
+import os
+
+from . import _build
+
+AF_OK, AF_ERR_ARG, AF_ERR_CUDA, AF_ERR_ALLOC, AF_ERR_CFL, AF_ERR_NONPHYSICAL, \
+    AF_ERR_NONFINITE, AF_ERR_STATE = range(8)
+AF_FP64, AF_FP32, AF_FP32_COMP = 0, 1, 2
+AF_TAI, AF_RB = 0, 1
+AF_HOST, AF_DEVICE = 0, 1
+AF_NINV = 12
+INVARIANT_NAMES = ["mass", "mom_x", "mom_y", "energy", "entropy_simpson", "entropy_avg",
+                   "kinetic_energy", "max_wave_speed", "min_rho", "min_p",
+                   "vorticity_integral", "flags"]
+PRECISIONS = {"fp64": AF_FP64, "fp32": AF_FP32, "fp32_comp": AF_FP32_COMP}
+VARIANTS = {"tai": AF_TAI, "rb": AF_RB}
+
+LIB_PATH = _build.LIB
+
+
+class AfGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("h", ctypes.c_double)]
+
+
+class AfState(ctypes.Structure):
+    _fields_ = [("avg", ctypes.c_void_p * 4), ("vtx", ctypes.c_void_p * 4),
+                ("ev", ctypes.c_void_p * 4), ("eh", ctypes.c_void_p * 4)]
+
+
+class AfError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, af_status_string(status), status))
+
+
+_lib = None
+
+
+def load():
+    """Load libaf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libaf.so not built: run paper_2605_12915_gb300._build.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        lib.af_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(AfGrid), d,
+                                ctypes.POINTER(AfState), ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, vp]
+        lib.af_init.restype = ctypes.c_int
+        lib.af_step.argtypes = [vp, d, i32]
+        lib.af_step.restype = ctypes.c_int
+        lib.af_sync.argtypes = [vp]
+        lib.af_sync.restype = ctypes.c_int
+        lib.af_get_state.argtypes = [vp, ctypes.POINTER(AfState), ctypes.c_int]
+        lib.af_get_state.restype = ctypes.c_int
+        lib.af_set_state.argtypes = [vp, ctypes.POINTER(AfState), ctypes.c_int]
+        lib.af_set_state.restype = ctypes.c_int
+        lib.af_reduce_invariants.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.af_reduce_invariants.restype = ctypes.c_int
+        lib.af_destroy.argtypes = [vp]
+        lib.af_destroy.restype = None
+        lib.af_status_string.argtypes = [ctypes.c_int]
+        lib.af_status_string.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+# ---- raw C-ABI functions, same names -----------------------------------------
+def af_status_string(status):
+    return load().af_status_string(int(status)).decode()
+
+
+def _state_struct(base_ptr, n):
+    """AfState whose 16 planes are consecutive blocks of n doubles from base_ptr."""
+    s = AfState()
+    for k in range(4):
+        s.avg[k] = base_ptr + 8 * n * k
+        s.vtx[k] = base_ptr + 8 * n * (4 + k)
+        s.ev[k] = base_ptr + 8 * n * (8 + k)
+        s.eh[k] = base_ptr + 8 * n * (12 + k)
+    return s
+
+
+def _array_ptr(arr):
+    """(pointer, on_device) of a C-contiguous float64 (16, ny, nx) numpy array or
+    torch tensor."""
+    if hasattr(arr, "data_ptr"):  # torch tensor
+        import torch
+        assert arr.dtype == torch.float64 and arr.is_contiguous() and arr.dim() == 3 \
+            and arr.shape[0] == 16, "state must be a contiguous float64 (16, ny, nx) tensor"
+        return arr.data_ptr(), arr.is_cuda
+    import numpy as np
+    assert isinstance(arr, np.ndarray) and arr.dtype == np.float64 and arr.flags["C_CONTIGUOUS"] \
+        and arr.ndim == 3 and arr.shape[0] == 16, \
+        "state must be a C-contiguous float64 (16, ny, nx) array"
+    return arr.ctypes.data, False
+
+
+def af_init(nx, ny, h, gamma, state, precision=AF_FP32_COMP, variant=AF_TAI, stream=None):
+    """Returns an opaque handle (int).  state: (16, ny, nx) float64 numpy array or
+    torch tensor (host or cuda).  stream: torch.cuda.Stream, raw handle or None."""
+    ptr, dev = _array_ptr(state)
+    assert state.shape[1] == ny and state.shape[2] == nx
+    g = AfGrid(nx, ny, h)
+    st = _state_struct(ptr, nx * ny)
+    hnd = ctypes.c_void_p()
+    s = getattr(stream, "cuda_stream", stream)
+    rc = load().af_init(ctypes.byref(hnd), ctypes.byref(g), gamma, ctypes.byref(st),
+                        AF_DEVICE if dev else AF_HOST, precision, variant,
+                        ctypes.c_void_p(s) if s else None)
+    if rc != AF_OK:
+        raise AfError(rc, "af_init")
+    return hnd.value
+
+
+def af_step(handle, dt, n_steps=1):
+    return load().af_step(ctypes.c_void_p(handle), float(dt), int(n_steps))
+
+
+def af_sync(handle):
+    return load().af_sync(ctypes.c_void_p(handle))
+
+
+def af_get_state(handle, out):
+    ptr, dev = _array_ptr(out)
+    n = out.shape[1] * out.shape[2]
+    st = _state_struct(ptr, n)
+    return load().af_get_state(ctypes.c_void_p(handle), ctypes.byref(st),
+                               AF_DEVICE if dev else AF_HOST)
+
+
+def af_set_state(handle, state):
+    ptr, dev = _array_ptr(state)
+    n = state.shape[1] * state.shape[2]
+    st = _state_struct(ptr, n)
+    return load().af_set_state(ctypes.c_void_p(handle), ctypes.byref(st),
+                               AF_DEVICE if dev else AF_HOST)
+
+
+def af_reduce_invariants(handle, out):
+    """out: float64 numpy array of AF_NINV values (host)."""
+    import numpy as np
+    assert isinstance(out, np.ndarray) and out.dtype == np.float64 and out.size >= AF_NINV
+    return load().af_reduce_invariants(ctypes.c_void_p(handle),
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+def af_destroy(handle):
+    if handle:
+        load().af_destroy(ctypes.c_void_p(handle))
+
+
+# ---- convenience wrapper ---------------------------------------------------
+class Solver:
+    """One grid on the current CUDA device.
+
+    >>> s = Solver(grid, gamma, state, precision="fp32_comp")
+    >>> s.step(dt, 100); s.state()  # numpy (16, ny, nx) float64
+    """
+
+    def __init__(self, grid, gamma, state, precision="fp32_comp", variant="tai", stream=None):
+        self.nx, self.ny, self.h, self.gamma = grid.nx, grid.ny, grid.h, gamma
+        self.handle = af_init(grid.nx, grid.ny, grid.h, gamma, state,
+                              PRECISIONS.get(precision, precision),
+                              VARIANTS.get(variant, variant), stream)
+
+    def step(self, dt, n_steps=1):
+        rc = af_step(self.handle, dt, n_steps)
+        if rc != AF_OK:
+            raise AfError(rc, "af_step")
+
+    def sync(self):
+        rc = af_sync(self.handle)
+        if rc != AF_OK:
+            raise AfError(rc, "af_sync")
+
+    def state(self, out=None):
+        import numpy as np
+        if out is None:
+            out = np.empty((16, self.ny, self.nx))
+        rc = af_get_state(self.handle, out)
+        if rc != AF_OK:
+            raise AfError(rc, "af_get_state")
+        return out
+
+    def set_state(self, state):
+        rc = af_set_state(self.handle, state)
+        if rc != AF_OK:
+            raise AfError(rc, "af_set_state")
+
+    def invariants(self):
+        import numpy as np
+        out = np.zeros(AF_NINV)
+        rc = af_reduce_invariants(self.handle, out)
+        if rc != AF_OK:
+            raise AfError(rc, "af_reduce_invariants")
+        return out
+
+    def close(self):
+        if self.handle:
+            af_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

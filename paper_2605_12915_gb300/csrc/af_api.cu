@@ -1,0 +1,420 @@
+// af_api.cu -- C ABI of the RB-TAI Active Flux step on GB300 (include/af.h).
+// One handle = one grid on one device and one stream; the state lives in HBM as
+// structure-of-arrays planes (sixteen per state, four more lo planes for the
+// compensated averages), ping-ponged between steps.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/af.h"
+#include "af_common.cuh"
+#include "af_reduce.cuh"
+#include "af_ref_kernels.cuh"
+
+using namespace af;
+
+struct af_handle {
+  int device;
+  int nx, ny;
+  size_t N;
+  double h, gamma;
+  af_precision prec;
+  af_variant var;
+  cudaStream_t stream;
+  size_t esize;          // bytes per element (4 or 8)
+  void* arena;           // all device planes of this handle
+  void* state[2][20];    // ping-pong state planes: 16 (+4 lo)
+  int cur;               // index of the current state
+  void* scratch[48];     // wc 4, inc 24, half 12, fx 4, gy 4
+  double* staging;       // 16 FP64 planes for host/device exchange (lazy)
+  unsigned* d_flags;
+  unsigned* h_flags;     // pinned mirror, written asynchronously after each step
+  double* d_red;         // reduction partials + result
+  double* h_red;         // pinned
+  int red_blocks;
+  int broken;
+  int fused;             // 1: fused single-pass kernel for the FP32 modes
+};
+
+namespace {
+
+af_status map_flags(unsigned f) {
+  if (f & FLAG_NONFINITE) return AF_ERR_NONFINITE;
+  if (f & FLAG_NONPHYSICAL) return AF_ERR_NONPHYSICAL;
+  if (f & (FLAG_CFL | FLAG_REACH)) return AF_ERR_CFL;
+  return AF_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+Planes<T> planes_of(af_handle* h, int which) {
+  Planes<T> p;
+  void** s = h->state[which];
+  for (int k = 0; k < 4; ++k) p.avg[k] = (T*)s[k];
+  for (int f = 0; f < 3; ++f)
+    for (int k = 0; k < 4; ++k) p.pt[f][k] = (T*)s[4 + 4 * f + k];
+  for (int k = 0; k < 4; ++k) p.lo[k] = (T*)s[16 + k];
+  return p;
+}
+
+// ---- FP64 <-> working precision conversion ---------------------------------
+struct F64Planes {
+  const double* p[16];
+};
+struct F64Out {
+  double* p[16];
+};
+
+template <typename T, bool COMP>
+__global__ void k_import(F64Planes src, Planes<T> dst, size_t N) {
+  for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < N;
+       id += (size_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < 4; ++k) {
+      double x = src.p[k][id];
+      T hi = (T)x;
+      dst.avg[k][id] = hi;
+      if (COMP) dst.lo[k][id] = (T)(x - (double)hi);
+    }
+    for (int f = 0; f < 3; ++f)
+      for (int k = 0; k < 4; ++k) dst.pt[f][k][id] = (T)src.p[4 + 4 * f + k][id];
+  }
+}
+
+template <typename T, bool COMP>
+__global__ void k_export(Planes<T> src, F64Out dst, size_t N) {
+  for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < N;
+       id += (size_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < 4; ++k)
+      dst.p[k][id] = (double)src.avg[k][id] + (COMP ? (double)src.lo[k][id] : 0.0);
+    for (int f = 0; f < 3; ++f)
+      for (int k = 0; k < 4; ++k) dst.p[4 + 4 * f + k][id] = (double)src.pt[f][k][id];
+  }
+}
+
+int grid1d(size_t N) {
+  size_t b = (N + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+StepArgs<T> step_args(af_handle* h, double dt) {
+  StepArgs<T> a;
+  a.in = planes_of<T>(h, h->cur);
+  a.out = planes_of<T>(h, 1 - h->cur);
+  int s = 0;
+  for (int k = 0; k < 4; ++k) a.wc[k] = (T*)h->scratch[s++];
+  for (int t = 0; t < 2; ++t)
+    for (int f = 0; f < 4; ++f)
+      for (int k = 0; k < 3; ++k) a.inc[t][f][k] = (T*)h->scratch[s++];
+  for (int f = 0; f < 3; ++f)
+    for (int k = 0; k < 4; ++k) a.half[f][k] = (T*)h->scratch[s++];
+  for (int k = 0; k < 4; ++k) a.fx[k] = (T*)h->scratch[s++];
+  for (int k = 0; k < 4; ++k) a.gy[k] = (T*)h->scratch[s++];
+  a.flags = h->d_flags;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.h = (T)h->h;
+  a.dt = (T)dt;
+  a.gamma = (T)h->gamma;
+  a.gm1 = (T)(h->gamma - 1.0);
+  a.gm1inv = (T)(1.0 / (h->gamma - 1.0));
+  a.variant = (int)h->var;
+  return a;
+}
+
+template <typename T, bool COMP>
+void launch_ref_step(af_handle* h, double dt) {
+  StepArgs<T> a = step_args<T>(h, dt);
+  dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
+  cudaStream_t s = h->stream;
+  k_center<T, COMP><<<grd, blk, 0, s>>>(a);
+  k_acoustic<0, T><<<grd, blk, 0, s>>>(a);
+  k_acoustic<1, T><<<grd, blk, 0, s>>>(a);
+  k_acoustic<2, T><<<grd, blk, 0, s>>>(a);
+  k_acoustic<3, T><<<grd, blk, 0, s>>>(a);
+  k_points<0, T><<<grd, blk, 0, s>>>(a);
+  k_points<1, T><<<grd, blk, 0, s>>>(a);
+  k_points<2, T><<<grd, blk, 0, s>>>(a);
+  k_flux<T><<<grd, blk, 0, s>>>(a);
+  k_average<T, COMP><<<grd, blk, 0, s>>>(a);
+}
+
+void launch_step(af_handle* h, double dt) {
+  switch (h->prec) {
+    case AF_FP64: launch_ref_step<double, false>(h, dt); break;
+    case AF_FP32: launch_ref_step<float, false>(h, dt); break;
+    case AF_FP32_COMP: launch_ref_step<float, true>(h, dt); break;
+  }
+}
+
+af_status check_state_ptrs(const af_state_f64* s) {
+  if (!s) return AF_ERR_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (!s->avg[k] || !s->vtx[k] || !s->ev[k] || !s->eh[k]) return AF_ERR_ARG;
+  return AF_OK;
+}
+
+const double* plane_in(const af_state_f64* s, int p) {
+  if (p < 4) return s->avg[p];
+  if (p < 8) return s->vtx[p - 4];
+  if (p < 12) return s->ev[p - 8];
+  return s->eh[p - 12];
+}
+
+af_status ensure_staging(af_handle* h) {
+  if (h->staging) return AF_OK;
+  if (cudaMalloc(&h->staging, sizeof(double) * 16 * h->N) != cudaSuccess) {
+    h->staging = nullptr;
+    return AF_ERR_ALLOC;
+  }
+  return AF_OK;
+}
+
+af_status cuda_fail(af_handle* h) {
+  if (h) h->broken = 1;
+  return AF_ERR_CUDA;
+}
+
+af_status import_state(af_handle* h, const af_state_f64* in, af_memory where) {
+  F64Planes src;
+  if (where == AF_HOST) {
+    af_status st = ensure_staging(h);
+    if (st != AF_OK) return st;
+    for (int p = 0; p < 16; ++p) {
+      if (cudaMemcpyAsync(h->staging + (size_t)p * h->N, plane_in(in, p), sizeof(double) * h->N,
+                          cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return cuda_fail(h);
+      src.p[p] = h->staging + (size_t)p * h->N;
+    }
+  } else {
+    for (int p = 0; p < 16; ++p) src.p[p] = plane_in(in, p);
+  }
+  int g = grid1d(h->N);
+  switch (h->prec) {
+    case AF_FP64: k_import<double, false><<<g, 256, 0, h->stream>>>(src, planes_of<double>(h, h->cur), h->N); break;
+    case AF_FP32: k_import<float, false><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N); break;
+    case AF_FP32_COMP: k_import<float, true><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N); break;
+  }
+  if (cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned), h->stream) != cudaSuccess) return cuda_fail(h);
+  if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
+  *(volatile unsigned*)h->h_flags = 0;
+  return AF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* af_status_string(af_status s) {
+  switch (s) {
+    case AF_OK: return "ok";
+    case AF_ERR_ARG: return "invalid argument";
+    case AF_ERR_CUDA: return "CUDA runtime error";
+    case AF_ERR_ALLOC: return "allocation failed";
+    case AF_ERR_CFL: return "time step too large: acoustic CFL above 1/2 or convective foot beyond one cell";
+    case AF_ERR_NONPHYSICAL: return "non-positive density or pressure";
+    case AF_ERR_NONFINITE: return "non-finite value in the state";
+    case AF_ERR_STATE: return "handle unusable after a CUDA error";
+  }
+  return "unknown status";
+}
+
+af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_state_f64* state,
+                  af_memory where, af_precision prec, af_variant var, void* cuda_stream) {
+  if (!out) return AF_ERR_ARG;
+  *out = nullptr;
+  if (!g || g->nx < 2 || g->ny < 2 || !(g->h > 0.0) || !(gamma > 1.0)) return AF_ERR_ARG;
+  if (prec != AF_FP64 && prec != AF_FP32 && prec != AF_FP32_COMP) return AF_ERR_ARG;
+  if (var != AF_TAI && var != AF_RB) return AF_ERR_ARG;
+  if (where != AF_HOST && where != AF_DEVICE) return AF_ERR_ARG;
+  if (check_state_ptrs(state) != AF_OK) return AF_ERR_ARG;
+  if ((int64_t)g->nx * (int64_t)g->ny > (int64_t)1 << 31) return AF_ERR_ARG;
+
+  af_handle* h = new (std::nothrow) af_handle();
+  if (!h) return AF_ERR_ALLOC;
+  memset(h, 0, sizeof(*h));
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return AF_ERR_CUDA;
+  }
+  h->nx = g->nx;
+  h->ny = g->ny;
+  h->N = (size_t)g->nx * g->ny;
+  h->h = g->h;
+  h->gamma = gamma;
+  h->prec = prec;
+  h->var = var;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->esize = prec == AF_FP64 ? 8 : 4;
+  h->fused = 0;
+  // 2 x 20 state planes + 48 scratch planes, each padded to 256 bytes
+  size_t plane = (h->N * h->esize + 255) & ~(size_t)255;
+  size_t nplanes = 2 * 20 + 48;
+  if (cudaMalloc(&h->arena, plane * nplanes) != cudaSuccess) {
+    delete h;
+    return AF_ERR_ALLOC;
+  }
+  char* base = (char*)h->arena;
+  for (int s = 0; s < 2; ++s)
+    for (int p = 0; p < 20; ++p) h->state[s][p] = base + plane * (size_t)(20 * s + p);
+  for (int p = 0; p < 48; ++p) h->scratch[p] = base + plane * (size_t)(40 + p);
+  h->red_blocks = 152 * 4;
+  bool ok = cudaMalloc(&h->d_flags, sizeof(unsigned)) == cudaSuccess &&
+            cudaMallocHost(&h->h_flags, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&h->d_red, sizeof(double) * (RED_VALS * h->red_blocks + AF_NINV)) ==
+                cudaSuccess &&
+            cudaMallocHost(&h->h_red, sizeof(double) * AF_NINV) == cudaSuccess;
+  if (!ok) {
+    af_destroy(h);
+    return AF_ERR_ALLOC;
+  }
+  if (prec == AF_FP32_COMP || prec == AF_FP32) {
+    // zero the lo planes once (unused in AF_FP32)
+    for (int s = 0; s < 2; ++s)
+      for (int k = 16; k < 20; ++k) cudaMemsetAsync(h->state[s][k], 0, plane, h->stream);
+  }
+  af_status st = import_state(h, state, where);
+  if (st != AF_OK) {
+    af_destroy(h);
+    return st;
+  }
+  *out = h;
+  return AF_OK;
+}
+
+af_status af_step(af_handle* h, double dt, int32_t n_steps) {
+  if (!h) return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  if (!(dt > 0.0) || n_steps < 0) return AF_ERR_ARG;
+  af_status prior = map_flags(*(volatile unsigned*)h->h_flags);
+  if (prior != AF_OK) return prior;
+  DeviceGuard guard(h->device);
+  for (int n = 0; n < n_steps; ++n) {
+    launch_step(h, dt);
+    h->cur = 1 - h->cur;
+  }
+  if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+  if (cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess)
+    return cuda_fail(h);
+  return AF_OK;
+}
+
+af_status af_sync(af_handle* h) {
+  if (!h) return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  DeviceGuard guard(h->device);
+  if (cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return cuda_fail(h);
+  return map_flags(*(volatile unsigned*)h->h_flags);
+}
+
+af_status af_set_state(af_handle* h, const af_state_f64* in, af_memory where) {
+  if (!h || check_state_ptrs(in) != AF_OK || (where != AF_HOST && where != AF_DEVICE))
+    return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  DeviceGuard guard(h->device);
+  return import_state(h, in, where);
+}
+
+af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
+  if (!h || check_state_ptrs(out) != AF_OK || (where != AF_HOST && where != AF_DEVICE))
+    return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  DeviceGuard guard(h->device);
+  F64Out dst;
+  if (where == AF_HOST) {
+    af_status st = ensure_staging(h);
+    if (st != AF_OK) return st;
+    for (int p = 0; p < 16; ++p) dst.p[p] = h->staging + (size_t)p * h->N;
+  } else {
+    for (int p = 0; p < 16; ++p) dst.p[p] = (double*)plane_in(out, p);
+  }
+  int g = grid1d(h->N);
+  switch (h->prec) {
+    case AF_FP64: k_export<double, false><<<g, 256, 0, h->stream>>>(planes_of<double>(h, h->cur), dst, h->N); break;
+    case AF_FP32: k_export<float, false><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N); break;
+    case AF_FP32_COMP: k_export<float, true><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N); break;
+  }
+  if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+  if (where == AF_HOST) {
+    for (int p = 0; p < 16; ++p)
+      if (cudaMemcpyAsync((void*)plane_in(out, p), dst.p[p], sizeof(double) * h->N,
+                          cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return cuda_fail(h);
+  }
+  return af_sync(h);
+}
+
+af_status af_reduce_invariants(af_handle* h, double* out) {
+  if (!h || !out) return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  DeviceGuard guard(h->device);
+  double* partial = h->d_red;
+  double* res = h->d_red + (size_t)RED_VALS * h->red_blocks;
+  dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
+  if (h->prec == AF_FP64) {
+    StepArgs<double> a = step_args<double>(h, 1.0);
+    k_center<double, false><<<grd, blk, 0, h->stream>>>(a);
+    RedArgs<double> r;
+    r.st = a.in;
+    for (int k = 0; k < 4; ++k) r.wc[k] = a.wc[k];
+    r.nx = h->nx; r.ny = h->ny; r.gamma = h->gamma; r.h = h->h; r.partial = partial;
+    k_inv_partial<double, false><<<h->red_blocks, RED_THREADS, 0, h->stream>>>(r);
+  } else {
+    StepArgs<float> a = step_args<float>(h, 1.0);
+    RedArgs<float> r;
+    r.st = a.in;
+    for (int k = 0; k < 4; ++k) r.wc[k] = a.wc[k];
+    r.nx = h->nx; r.ny = h->ny; r.gamma = h->gamma; r.h = h->h; r.partial = partial;
+    if (h->prec == AF_FP32_COMP) {
+      k_center<float, true><<<grd, blk, 0, h->stream>>>(a);
+      k_inv_partial<float, true><<<h->red_blocks, RED_THREADS, 0, h->stream>>>(r);
+    } else {
+      k_center<float, false><<<grd, blk, 0, h->stream>>>(a);
+      k_inv_partial<float, false><<<h->red_blocks, RED_THREADS, 0, h->stream>>>(r);
+    }
+  }
+  k_inv_final<<<1, 32, 0, h->stream>>>(partial, h->red_blocks, h->h, res);
+  if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+  if (cudaMemcpyAsync(h->h_red, res, sizeof(double) * (AF_NINV - 1), cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess)
+    return cuda_fail(h);
+  af_status st = af_sync(h);
+  if (st == AF_ERR_CUDA || st == AF_ERR_STATE) return st;
+  for (int k = 0; k < AF_NINV - 1; ++k) out[k] = h->h_red[k];
+  out[AF_INV_FLAGS] = (double)*(volatile unsigned*)h->h_flags;
+  return st;
+}
+
+void af_destroy(af_handle* h) {
+  if (!h) return;
+  DeviceGuard guard(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->arena) cudaFree(h->arena);
+  if (h->staging) cudaFree(h->staging);
+  if (h->d_flags) cudaFree(h->d_flags);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  if (h->d_red) cudaFree(h->d_red);
+  if (h->h_red) cudaFreeHost(h->h_red);
+  delete h;
+}
+
+}  // extern "C"

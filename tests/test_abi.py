@@ -1,0 +1,134 @@
+"""Host-side checks of the CUDA library (no GPU needed): it builds for sm_103a,
+loads, and exports every entry point include/af.h declares; the committed
+generated stencil header is what its generator writes; and the generated
+stencil tables, applied on the CPU, reproduce the oracle's acoustic operator.
+"""
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "af.h")
+CSRC = os.path.join(ROOT, "paper_2605_12915_gb300", "csrc")
+STENCILS = os.path.join(CSRC, "af_stencils.cuh")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(af_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libaf():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2605_12915_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_library_exports_every_declared_entry_point(libaf):
+    syms = declared_symbols()
+    assert {"af_init", "af_step", "af_reduce_invariants", "af_destroy"} <= set(syms)
+    missing = [s for s in syms if not hasattr(libaf, s)]
+    assert not missing, missing
+
+
+def test_status_strings(libaf):
+    libaf.af_status_string.restype = ctypes.c_char_p
+    for s in range(8):
+        assert libaf.af_status_string(s)
+
+
+def test_init_rejects_bad_arguments_without_touching_the_gpu(libaf):
+    from paper_2605_12915_gb300 import AfGrid, AfState, AF_ERR_ARG
+    h = ctypes.c_void_p()
+    g = AfGrid(1, 4, 0.1)  # nx < 2
+    st = AfState()
+    rc = libaf.af_init(ctypes.byref(h), ctypes.byref(g), ctypes.c_double(1.4), ctypes.byref(st),
+                       0, 0, 0, None)
+    assert rc == AF_ERR_ARG and not h.value
+
+
+@pytest.mark.slow
+def test_committed_stencils_match_generator(tmp_path):
+    pytest.importorskip("sympy")
+    out = tmp_path / "af_stencils.cuh"
+    subprocess.check_call(["python", os.path.join(CSRC, "gen_stencils.py"), str(out)],
+                          stdout=subprocess.DEVNULL)
+    assert out.read_text() == open(STENCILS).read()
+
+
+# ---- apply the generated tables on the CPU ---------------------------------
+def parse_stencils():
+    """{family: [(a, b, combo, field, dst, o, q, value)]} from the generated code."""
+    fams = {}
+    fam = None
+    orbit = None
+    for line in open(STENCILS):
+        m = re.match(r"__device__ __forceinline__ void af_sac_(\w+)\(", line)
+        if m:
+            fam = m.group(1)
+            fams[fam] = []
+        m = re.search(r"orbit \(\+-(\d+), \+-(\d+)\)", line)
+        if m:
+            orbit = (int(m.group(1)), int(m.group(2)))
+        m = re.search(r"(Gp|Guv)\[(\d)\]\[(\d)\] = fma\(T\(([-0-9.e]+)\), (ee|eo|oe|oo)(p|u|v),",
+                      line)
+        if m:
+            fams[fam].append((orbit[0], orbit[1], m.group(5), m.group(6), m.group(1),
+                              int(m.group(2)), int(m.group(3)) + 1, float(m.group(4))))
+    return fams
+
+
+def apply_tables(entries, lat, K):
+    """G[o][q] for lattice data lat[(dx, dy)] = (p, u, v) around node value K."""
+    Gp = np.zeros((3, 5))
+    Guv = np.zeros((3, 5))
+    fidx = {"p": 0, "u": 1, "v": 2}
+    for a, b, combo, f, dst, o, q, val in entries:
+        k = fidx[f]
+        members = {(sx * a, sy * b) for sx in (1, -1) for sy in (1, -1)}
+        tot = 0.0
+        for (dx, dy) in members:
+            sx = 1 if dx >= 0 else -1
+            sy = 1 if dy >= 0 else -1
+            wx = sx if combo[0] == "o" else 1
+            wy = sy if combo[1] == "o" else 1
+            dev = lat[(dx, dy)][k] - (K[k] if combo == "ee" else 0.0)
+            tot += wx * wy * dev
+        (Gp if dst == "Gp" else Guv)[o, q] += val * tot
+    return Gp, Guv
+
+
+@pytest.mark.parametrize("fam_name,fam", [("V", 0), ("EV", 1), ("EH", 2), ("C", 3)])
+def test_generated_tables_match_oracle_operator(orc, fam_name, fam):
+    from test_oracle_acoustic import cells_from_fn
+    tables = parse_stencils()[fam_name]
+    rng = np.random.default_rng(21 + fam)
+    lat = {}
+    Z = 1.45
+
+    def val(X, Y):
+        key = (round(2 * X), round(2 * Y))
+        if key not in lat:
+            lat[key] = rng.normal(size=3)
+        return lat[key]
+
+    cells = cells_from_fn(fam, lambda k, X, Y: val(X, Y))
+    K = lat[(0, 0)]
+    Gp, Guv = apply_tables(tables, lat, K)
+    for r in (0.1, 0.3, 0.5):
+        want = orc.sac_node(fam, cells, r, Z)  # (p_ac, u_ac, v_ac)
+        pw = np.array([r ** q for q in range(5)])
+        dp = np.sum(pw * (Gp[0] + Z * Guv[0]))
+        du = np.sum(pw * (Gp[1] / Z + Guv[1]))
+        dv = np.sum(pw * (Gp[2] / Z + Guv[2]))
+        got = np.array([K[0] + dp, K[1] + du, K[2] + dv])
+        assert np.max(np.abs(got - want)) < 1e-12, (r, got, want)

@@ -1,0 +1,167 @@
+"""GPU parity: the CUDA step through the C ABI against the FP64 CPU oracle on the
+same seeded inputs (element by element), plus FP32 against FP64, conservation,
+determinism and error reporting.
+
+Tolerances (relative L-inf, per plane: max |a - b| / max |b|):
+  FP64 GPU vs oracle after up to 100 steps ...... 1e-12
+  FP32 / FP32+compensated vs FP64 after 100 steps  2e-5
+"""
+import numpy as np
+import pytest
+
+import paper_2605_12915_gb300 as af
+from paper_2605_12915_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+def rel_linf(a, b):
+    num = np.max(np.abs(a - b), axis=(1, 2))
+    den = np.maximum(np.max(np.abs(b), axis=(1, 2)), 1e-300)
+    return float(np.max(num / den))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    af._build.build()
+    af.load()
+
+
+def run_gpu(P, n_steps, precision="fp64", variant="tai", dt=None):
+    s = af.Solver(P.grid, P.gamma, P.state, precision=precision, variant=variant)
+    s.step(P.dt if dt is None else dt, n_steps)
+    out = s.state()
+    s.close()
+    return out
+
+
+def run_orc(orc, P, n_steps, variant=0, dt=None):
+    st, fl = orc.run(P.state, P.grid.h, P.gamma, P.dt if dt is None else dt, n_steps, variant)
+    assert fl == 0
+    return st
+
+
+@pytest.mark.parametrize("variant", ["tai", "rb"])
+@pytest.mark.parametrize("shape", [(8, 8), (37, 29), (70, 33)])
+def test_fp64_matches_oracle_random(orc, shape, variant):
+    """Ragged sizes spanning several thread blocks; 20 steps."""
+    nx, ny = shape
+    P = I.random_smooth(nx, ny, seed=nx + ny, amp=0.06)
+    dt = P.dt * (0.6 if variant == "rb" else 1.0)
+    got = run_gpu(P, 20, "fp64", variant, dt)
+    want = run_orc(orc, P, 20, 0 if variant == "tai" else 1, dt)
+    assert rel_linf(got, want) < TOL64
+
+
+def test_fp64_matches_oracle_vortex_100_steps(orc):
+    """Isentropic vortex, 32^2, CFL 0.4, 100 steps, FP64, transported update."""
+    P = I.vortex(n=32)
+    got = run_gpu(P, 100, "fp64")
+    want = run_orc(orc, P, 100)
+    err = rel_linf(got, want)
+    print("vortex fp64 vs oracle rel Linf", err)
+    assert err < TOL64
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
+def test_fp32_vs_fp64_vortex_100_steps(precision):
+    P = I.vortex(n=32)
+    a = run_gpu(P, 100, precision)
+    b = run_gpu(P, 100, "fp64")
+    err = rel_linf(a, b)
+    print("vortex", precision, "vs fp64 rel Linf", err)
+    assert err < TOL32
+
+
+def test_pulse_512_one_step_matches_oracle(orc):
+    """Gaussian pulse at its full size (512^2): one step, whole grid, FP64."""
+    P = I.pulse(n=512)
+    got = run_gpu(P, 1, "fp64")
+    want = run_orc(orc, P, 1)
+    assert rel_linf(got, want) < TOL64
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
+def test_pulse_512_fp32_vs_fp64_100_steps(precision):
+    P = I.pulse(n=512)
+    a = run_gpu(P, 100, precision)
+    b = run_gpu(P, 100, "fp64")
+    err = rel_linf(a, b)
+    print("pulse", precision, "vs fp64 rel Linf", err)
+    assert err < TOL32
+
+
+def test_free_stream(orc):
+    P = I.uniform(33, 17)
+    for prec, tol in (("fp64", 1e-14), ("fp32", 1e-6), ("fp32_comp", 1e-6)):
+        out = run_gpu(P, 10, prec)
+        assert rel_linf(out, P.state) < tol, prec
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32_comp", 1e-12)])
+def test_conservation(precision, tol):
+    P = I.random_smooth(64, 48, seed=5, amp=0.05)
+    s = af.Solver(P.grid, P.gamma, P.state, precision=precision)
+    inv0 = s.invariants()
+    s.step(P.dt, 100)
+    inv1 = s.invariants()
+    s.close()
+    scale = np.array([inv0[0], inv0[0], inv0[0], inv0[3]])
+    drift = np.abs(inv1[:4] - inv0[:4]) / scale
+    print(precision, "conservation drift", drift)
+    assert np.all(drift < tol), drift
+
+
+def test_invariants_match_oracle(orc):
+    P = I.random_smooth(40, 24, seed=8, amp=0.05)
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp64")
+    s.step(P.dt, 5)
+    st = s.state()
+    got = s.invariants()
+    s.close()
+    want = orc.invariants(st, P.grid.h, P.gamma)
+    for k in range(11):
+        scale = max(abs(want[k]), 1e-12 if k == 10 else 1.0)
+        assert abs(got[k] - want[k]) <= 1e-12 * scale, (af.INVARIANT_NAMES[k], got[k], want[k])
+
+
+def test_deterministic():
+    P = I.random_smooth(96, 64, seed=2)
+    a = run_gpu(P, 10, "fp32_comp")
+    b = run_gpu(P, 10, "fp32_comp")
+    assert np.array_equal(a, b)
+
+
+def test_errors_are_reported():
+    P = I.random_smooth(16, 16, seed=1)
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp32")
+    assert af.af_step(s.handle, P.dt * 3.0, 1) == af.AF_OK  # asynchronous
+    assert af.af_sync(s.handle) == af.AF_ERR_CFL
+    assert af.af_step(s.handle, P.dt, 1) == af.AF_ERR_CFL  # latched
+    s.set_state(P.state)  # clears the latch
+    assert af.af_step(s.handle, P.dt, 1) == af.AF_OK
+    assert af.af_sync(s.handle) == af.AF_OK
+    bad = P.state.copy()
+    bad[7, 3, 4] = -1.0  # negative vertex pressure
+    s.set_state(bad)
+    af.af_step(s.handle, P.dt, 1)
+    assert af.af_sync(s.handle) == af.AF_ERR_NONPHYSICAL
+    s.close()
+    assert af.af_step(0, 0.1, 1) == af.AF_ERR_ARG
+
+
+def test_device_tensors_and_stream():
+    torch = pytest.importorskip("torch")
+    P = I.random_smooth(48, 40, seed=3)
+    st = torch.from_numpy(P.state).cuda()
+    stream = torch.cuda.Stream()
+    s = af.Solver(P.grid, P.gamma, st, precision="fp64", stream=stream)
+    s.step(P.dt, 3)
+    out = torch.empty_like(st)
+    s.state(out)
+    host = run_gpu(P, 3, "fp64")
+    assert np.array_equal(out.cpu().numpy(), host)
+    s.close()
