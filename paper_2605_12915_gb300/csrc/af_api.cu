@@ -13,6 +13,7 @@
 #include "af_common.cuh"
 #include "af_reduce.cuh"
 #include "af_ref_kernels.cuh"
+#include "af_fused.cuh"
 
 using namespace af;
 
@@ -42,8 +43,8 @@ struct af_handle {
 namespace {
 
 af_status map_flags(unsigned f) {
-  if (f & FLAG_NONFINITE) return AF_ERR_NONFINITE;
   if (f & FLAG_NONPHYSICAL) return AF_ERR_NONPHYSICAL;
+  if (f & FLAG_NONFINITE) return AF_ERR_NONFINITE;
   if (f & (FLAG_CFL | FLAG_REACH)) return AF_ERR_CFL;
   return AF_OK;
 }
@@ -156,8 +157,14 @@ void launch_ref_step(af_handle* h, double dt) {
 void launch_step(af_handle* h, double dt) {
   switch (h->prec) {
     case AF_FP64: launch_ref_step<double, false>(h, dt); break;
-    case AF_FP32: launch_ref_step<float, false>(h, dt); break;
-    case AF_FP32_COMP: launch_ref_step<float, true>(h, dt); break;
+    case AF_FP32:
+      if (h->fused) launch_fused_step<false>(h->stream, step_args<float>(h, dt));
+      else launch_ref_step<float, false>(h, dt);
+      break;
+    case AF_FP32_COMP:
+      if (h->fused) launch_fused_step<true>(h->stream, step_args<float>(h, dt));
+      else launch_ref_step<float, true>(h, dt);
+      break;
   }
 }
 
@@ -261,7 +268,10 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
   h->var = var;
   h->stream = (cudaStream_t)cuda_stream;
   h->esize = prec == AF_FP64 ? 8 : 4;
-  h->fused = 0;
+  // FP32 modes run the fused single-pass kernel; AF_PATH=ref selects the
+  // multi-kernel path (same arithmetic, intermediate values in HBM).
+  const char* path = getenv("AF_PATH");
+  h->fused = (prec != AF_FP64) && !(path && strcmp(path, "ref") == 0);
   // 2 x 20 state planes + 48 scratch planes, each padded to 256 bytes
   size_t plane = (h->N * h->esize + 255) & ~(size_t)255;
   size_t nplanes = 2 * 20 + 48;
