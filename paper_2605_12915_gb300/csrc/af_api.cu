@@ -22,6 +22,7 @@ struct af_handle {
   int nx, ny;
   size_t N;
   double h, gamma;
+  double rho_ref, p_ref;  // storage offsets of density and pressure (0 in FP64)
   af_precision prec;
   af_variant var;
   cudaStream_t stream;
@@ -79,30 +80,44 @@ struct F64Out {
   double* p[16];
 };
 
+struct Offsets {
+  double rho, p, e;  // subtracted from rho, p and the energy average on import
+};
+
 template <typename T, bool COMP>
-__global__ void k_import(F64Planes src, Planes<T> dst, size_t N) {
+__global__ void k_import(F64Planes src, Planes<T> dst, size_t N, Offsets o) {
   for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < N;
        id += (size_t)gridDim.x * blockDim.x) {
     for (int k = 0; k < 4; ++k) {
-      double x = src.p[k][id];
+      double x = src.p[k][id] - (k == 0 ? o.rho : (k == 3 ? o.e : 0.0));
       T hi = (T)x;
       dst.avg[k][id] = hi;
       if (COMP) dst.lo[k][id] = (T)(x - (double)hi);
     }
     for (int f = 0; f < 3; ++f)
-      for (int k = 0; k < 4; ++k) dst.pt[f][k][id] = (T)src.p[4 + 4 * f + k][id];
+      for (int k = 0; k < 4; ++k)
+        dst.pt[f][k][id] =
+            (T)(src.p[4 + 4 * f + k][id] - (k == 0 ? o.rho : (k == 3 ? o.p : 0.0)));
   }
 }
 
 template <typename T, bool COMP>
-__global__ void k_export(Planes<T> src, F64Out dst, size_t N) {
+__global__ void k_export(Planes<T> src, F64Out dst, size_t N, Offsets o) {
   for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < N;
        id += (size_t)gridDim.x * blockDim.x) {
     for (int k = 0; k < 4; ++k)
-      dst.p[k][id] = (double)src.avg[k][id] + (COMP ? (double)src.lo[k][id] : 0.0);
+      dst.p[k][id] = ((double)src.avg[k][id] + (COMP ? (double)src.lo[k][id] : 0.0)) +
+                     (k == 0 ? o.rho : (k == 3 ? o.e : 0.0));
     for (int f = 0; f < 3; ++f)
-      for (int k = 0; k < 4; ++k) dst.p[4 + 4 * f + k][id] = (double)src.pt[f][k][id];
+      for (int k = 0; k < 4; ++k)
+        dst.p[4 + 4 * f + k][id] =
+            (double)src.pt[f][k][id] + (k == 0 ? o.rho : (k == 3 ? o.p : 0.0));
   }
+}
+
+Offsets offsets_of(const af_handle* h) {
+  Offsets o = {h->rho_ref, h->p_ref, h->p_ref / (h->gamma - 1.0)};
+  return o;
 }
 
 int grid1d(size_t N) {
@@ -130,9 +145,12 @@ StepArgs<T> step_args(af_handle* h, double dt) {
   a.ny = h->ny;
   a.h = (T)h->h;
   a.dt = (T)dt;
-  a.gamma = (T)h->gamma;
-  a.gm1 = (T)(h->gamma - 1.0);
-  a.gm1inv = (T)(1.0 / (h->gamma - 1.0));
+  a.gas.gamma = (T)h->gamma;
+  a.gas.gm1 = (T)(h->gamma - 1.0);
+  a.gas.gm1inv = (T)(1.0 / (h->gamma - 1.0));
+  a.gas.g_gm1 = (T)(h->gamma / (h->gamma - 1.0));
+  a.gas.rho_ref = (T)h->rho_ref;
+  a.gas.p_ref = (T)h->p_ref;
   a.variant = (int)h->var;
   return a;
 }
@@ -212,9 +230,9 @@ af_status import_state(af_handle* h, const af_state_f64* in, af_memory where) {
   }
   int g = grid1d(h->N);
   switch (h->prec) {
-    case AF_FP64: k_import<double, false><<<g, 256, 0, h->stream>>>(src, planes_of<double>(h, h->cur), h->N); break;
-    case AF_FP32: k_import<float, false><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N); break;
-    case AF_FP32_COMP: k_import<float, true><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N); break;
+    case AF_FP64: k_import<double, false><<<g, 256, 0, h->stream>>>(src, planes_of<double>(h, h->cur), h->N, offsets_of(h)); break;
+    case AF_FP32: k_import<float, false><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N, offsets_of(h)); break;
+    case AF_FP32_COMP: k_import<float, true><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N, offsets_of(h)); break;
   }
   if (cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned), h->stream) != cudaSuccess) return cuda_fail(h);
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
@@ -298,6 +316,22 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
     for (int s = 0; s < 2; ++s)
       for (int k = 16; k < 20; ++k) cudaMemsetAsync(h->state[s][k], 0, plane, h->stream);
   }
+  // storage offsets: the initial vertex state at (0,0) (FP32 modes only)
+  if (prec != AF_FP64) {
+    double r0 = 0.0, p0 = 0.0;
+    if (where == AF_HOST) {
+      r0 = state->vtx[0][0];
+      p0 = state->vtx[3][0];
+    } else if (cudaMemcpy(&r0, state->vtx[0], sizeof(double), cudaMemcpyDeviceToHost) !=
+                   cudaSuccess ||
+               cudaMemcpy(&p0, state->vtx[3], sizeof(double), cudaMemcpyDeviceToHost) !=
+                   cudaSuccess) {
+      af_destroy(h);
+      return AF_ERR_CUDA;
+    }
+    h->rho_ref = (r0 > 0.0 && r0 < 1e30) ? r0 : 0.0;
+    h->p_ref = (p0 > 0.0 && p0 < 1e30) ? p0 : 0.0;
+  }
   af_status st = import_state(h, state, where);
   if (st != AF_OK) {
     af_destroy(h);
@@ -359,9 +393,9 @@ af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
   }
   int g = grid1d(h->N);
   switch (h->prec) {
-    case AF_FP64: k_export<double, false><<<g, 256, 0, h->stream>>>(planes_of<double>(h, h->cur), dst, h->N); break;
-    case AF_FP32: k_export<float, false><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N); break;
-    case AF_FP32_COMP: k_export<float, true><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N); break;
+    case AF_FP64: k_export<double, false><<<g, 256, 0, h->stream>>>(planes_of<double>(h, h->cur), dst, h->N, offsets_of(h)); break;
+    case AF_FP32: k_export<float, false><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N, offsets_of(h)); break;
+    case AF_FP32_COMP: k_export<float, true><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N, offsets_of(h)); break;
   }
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
   if (where == AF_HOST) {
@@ -387,6 +421,7 @@ af_status af_reduce_invariants(af_handle* h, double* out) {
     r.st = a.in;
     for (int k = 0; k < 4; ++k) r.wc[k] = a.wc[k];
     r.nx = h->nx; r.ny = h->ny; r.gamma = h->gamma; r.h = h->h; r.partial = partial;
+    r.rho_ref = h->rho_ref; r.p_ref = h->p_ref; r.e_ref = h->p_ref / (h->gamma - 1.0);
     k_inv_partial<double, false><<<h->red_blocks, RED_THREADS, 0, h->stream>>>(r);
   } else {
     StepArgs<float> a = step_args<float>(h, 1.0);
@@ -394,6 +429,7 @@ af_status af_reduce_invariants(af_handle* h, double* out) {
     r.st = a.in;
     for (int k = 0; k < 4; ++k) r.wc[k] = a.wc[k];
     r.nx = h->nx; r.ny = h->ny; r.gamma = h->gamma; r.h = h->h; r.partial = partial;
+    r.rho_ref = h->rho_ref; r.p_ref = h->p_ref; r.e_ref = h->p_ref / (h->gamma - 1.0);
     if (h->prec == AF_FP32_COMP) {
       k_center<float, true><<<grd, blk, 0, h->stream>>>(a);
       k_inv_partial<float, true><<<h->red_blocks, RED_THREADS, 0, h->stream>>>(r);

@@ -41,44 +41,60 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 }
 
 // ---- gas model (Sec. 2) ---------------------------------------------------
+// Storage convention: density and pressure are held as offsets from a
+// per-grid reference state (rho_ref, p_ref), and the energy average as an
+// offset from p_ref/(gamma-1).  In FP32 this keeps the rounding of stored
+// values proportional to the flow's variations rather than to the absolute
+// pressure (low-Mach flows carry p ~ 1/(gamma M^2)); in FP64 the offsets are 0.
 template <typename T>
-__device__ __forceinline__ void cons_from_prim(const Prim<T>& w, T gm1inv, T u[4]) {
+struct Gas {
+  T gamma, gm1, gm1inv, g_gm1;  // gamma, gamma-1, 1/(gamma-1), gamma/(gamma-1)
+  T rho_ref, p_ref;
+};
+
+// conservative offsets (rho~, rho u, rho v, E~) of a stored primitive
+// (rho~, u, v, p~): E~ = E - p_ref/(gamma-1) = p~/(gamma-1) + rho |u|^2 / 2
+template <typename T>
+__device__ __forceinline__ void cons_from_stored(const Prim<T>& w, const Gas<T>& g, T u[4]) {
+  const T rho = g.rho_ref + w.r;
   u[0] = w.r;
-  u[1] = w.r * w.u;
-  u[2] = w.r * w.v;
-  u[3] = w.p * gm1inv + T(0.5) * w.r * (w.u * w.u + w.v * w.v);
+  u[1] = rho * w.u;
+  u[2] = rho * w.v;
+  u[3] = w.p * g.gm1inv + T(0.5) * rho * (w.u * w.u + w.v * w.v);
 }
 
 template <typename T>
-__device__ __forceinline__ Prim<T> prim_from_cons(const T u[4], T gm1) {
+__device__ __forceinline__ Prim<T> stored_from_cons(const T u[4], const Gas<T>& g) {
   Prim<T> w;
+  const T rho = g.rho_ref + u[0];
+  const T inv = T(1) / rho;
   w.r = u[0];
-  T inv = T(1) / u[0];
   w.u = u[1] * inv;
   w.v = u[2] * inv;
-  w.p = gm1 * (u[3] - T(0.5) * (u[1] * w.u + u[2] * w.v));
+  w.p = g.gm1 * (u[3] - T(0.5) * (u[1] * w.u + u[2] * w.v));
   return w;
 }
 
-// Euler fluxes F (x) and G (y) from a primitive state
+// Euler fluxes F (x) and G (y) of a stored primitive.  The constant p_ref is
+// left out of the momentum fluxes: it cancels in every flux difference.
 template <typename T>
-__device__ __forceinline__ void flux_x(const Prim<T>& w, T gm1inv, T f[4]) {
-  T e = w.p * gm1inv + T(0.5) * w.r * (w.u * w.u + w.v * w.v);
-  T m = w.r * w.u;
+__device__ __forceinline__ void flux_x(const Prim<T>& w, const Gas<T>& g, T f[4]) {
+  const T rho = g.rho_ref + w.r, p = g.p_ref + w.p;
+  const T m = rho * w.u;
   f[0] = m;
   f[1] = m * w.u + w.p;
   f[2] = m * w.v;
-  f[3] = w.u * (e + w.p);
+  f[3] = w.u * (p * g.g_gm1 + T(0.5) * rho * (w.u * w.u + w.v * w.v));
 }
 
 template <typename T>
-__device__ __forceinline__ void flux_y(const Prim<T>& w, T gm1inv, T g[4]) {
-  T e = w.p * gm1inv + T(0.5) * w.r * (w.u * w.u + w.v * w.v);
-  T m = w.r * w.v;
-  g[0] = m;
-  g[1] = m * w.u;
-  g[2] = m * w.v + w.p;
-  g[3] = w.v * (e + w.p);
+__device__ __forceinline__ void flux_y(const Prim<T>& w, const Gas<T>& g, T f[4]) {
+  const T rho = g.rho_ref + w.r, p = g.p_ref + w.p;
+  const T m = rho * w.v;
+  f[0] = m;
+  f[1] = m * w.u;
+  f[2] = m * w.v + w.p;
+  f[3] = w.v * (p * g.g_gm1 + T(0.5) * rho * (w.u * w.u + w.v * w.v));
 }
 
 // ---- Q2 Lagrange basis on nodes -1, 0, 1 (Sec. 4) ----------------------------
@@ -139,6 +155,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated average update: (hi, lo) <- (hi, lo) + (fl - fr) + (gb - gt),
+// with fl, fr, gb, gt the scaled edge terms shared with the neighbouring cells.
+// Every step before the last is error free (Knuth TwoSum), so each edge value
+// enters its two cells with opposite signs exactly and the only rounding is
+// that of the new lo word.
+__device__ __forceinline__ void comp_update(float& hi, float& lo, float fl, float fr, float gb,
+                                            float gt) {
+  float dx, ex, dy, ey, d, ed, s, es, t, et;
+  two_sum(fl, -fr, dx, ex);
+  two_sum(gb, -gt, dy, ey);
+  two_sum(dx, dy, d, ed);
+  two_sum(hi, d, s, es);
+  two_sum(lo, es, t, et);
+  t = __fadd_rn(t, __fadd_rn(et, __fadd_rn(ed, __fadd_rn(ex, ey))));
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
 }
 
 }  // namespace af

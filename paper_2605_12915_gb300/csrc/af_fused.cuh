@@ -156,17 +156,17 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
       float u[4];
-      cons_from_prim(as_prim(LW[cidx[n]]), a.gm1inv, u);
+      cons_from_stored(as_prim(LW[cidx[n]]), a.gas, u);
 #pragma unroll
       for (int k = 0; k < 4; ++k) c[k] += (ub[k] - u[k]) + lo[k];
-      cons_from_prim(as_prim(LW[eidx[n]]), a.gm1inv, u);
+      cons_from_stored(as_prim(LW[eidx[n]]), a.gas, u);
 #pragma unroll
       for (int k = 0; k < 4; ++k) e[k] += (ub[k] - u[k]) + lo[k];
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) uc[k] = (ub[k] + lo[k]) + (0.0625f * c[k] + 0.25f * e[k]);
-    Prim<float> w = prim_from_cons(uc, a.gm1);
-    if (!(w.r > 0.f && w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
+    Prim<float> w = stored_from_cons(uc, a.gas);
+    if (!(a.gas.rho_ref + w.r > 0.f && a.gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
     LW[b + FW + 1] = make_float4(w.r, w.u, w.v, w.p);
   }
   __syncthreads();
@@ -188,9 +188,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
       }
       const int node = (dy + 2) * FW + (dx + 2);
       const float4 wk4 = LW[node];
-      if (!(wk4.x > 0.f && wk4.w > 0.f)) bad |= FLAG_NONPHYSICAL;
-      const float c = sqrtf(a.gamma * wk4.w / wk4.x);
-      const float Z = wk4.x * c, Zinv = 1.f / Z;
+      const float rk = a.gas.rho_ref + wk4.x, pk = a.gas.p_ref + wk4.w;
+      if (!(rk > 0.f && pk > 0.f)) bad |= FLAG_NONPHYSICAL;
+      const float c = sqrtf(a.gas.gamma * pk / rk);
+      const float Z = rk * c, Zinv = 1.f / Z;
       const float r1 = c * a.dt / a.h;
       if (r1 > 0.5f) bad |= FLAG_CFL;
       float Gp[3][4], Guv[3][4];
@@ -256,15 +257,16 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
       if (a.variant == 0) {
         // transported increment at the foot, rho from dp / c_f^2 (Sec. 6.1 step 4)
         eval_d_s<DW>(LDs, (fcy - 2) * DW + (fcx - 2), xi, eta, d);
-        if (!(wf.r > 0.f && wf.p > 0.f)) bad |= FLAG_NONPHYSICAL;
-        nw.r = wf.r + d[2] * wf.r / (a.gamma * wf.p);
+        const float rf = a.gas.rho_ref + wf.r, pf = a.gas.p_ref + wf.p;
+        if (!(rf > 0.f && pf > 0.f)) bad |= FLAG_NONPHYSICAL;
+        nw.r = wf.r + d[2] * rf / (a.gas.gamma * pf);
       } else {
         // additive update (Eq. barsukow-additive), acoustic rho closure at P
         const float* dp = LDs + 3 * ((lyp - 2) * DW + (lxp - 2));
         d[0] = dp[0];
         d[1] = dp[1];
         d[2] = dp[2];
-        nw.r = wf.r + d[2] * wp.x / (a.gamma * wp.w);
+        nw.r = wf.r + d[2] * (a.gas.rho_ref + wp.x) / (a.gas.gamma * (a.gas.p_ref + wp.w));
       }
       nw.u = wf.u + d[0];
       nw.v = wf.v + d[1];
@@ -326,9 +328,9 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
       }
       float fa[4], fm[4], fb[4];
       if (vert) {
-        flux_x(wa, a.gm1inv, fa); flux_x(wm, a.gm1inv, fm); flux_x(wb, a.gm1inv, fb);
+        flux_x(wa, a.gas, fa); flux_x(wm, a.gas, fm); flux_x(wb, a.gas, fb);
       } else {
-        flux_y(wa, a.gm1inv, fa); flux_y(wm, a.gm1inv, fm); flux_y(wb, a.gm1inv, fb);
+        flux_y(wa, a.gas, fa); flux_y(wm, a.gas, fm); flux_y(wb, a.gas, fb);
       }
       const float wt = s == 1 ? 4.f : 1.f;
 #pragma unroll
@@ -357,16 +359,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
     for (int c = 0; c < 4; ++c) {
       const float* Fc = FLX + c * NE;
       if (COMP) {
-        float hi = __ldg(a.in.avg[c] + id), lo = __ldg(a.in.lo[c] + id), e;
-        const float terms[4] = {Fc[fl], -Fc[fr], Fc[gb], -Fc[gt]};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          two_sum(hi, terms[q], hi, e);
-          lo = __fadd_rn(lo, e);
-        }
-        const float sum = __fadd_rn(hi, lo);
-        lo = __fsub_rn(lo, __fsub_rn(sum, hi));
-        hi = sum;
+        float hi = __ldg(a.in.avg[c] + id), lo = __ldg(a.in.lo[c] + id);
+        comp_update(hi, lo, Fc[fl], Fc[fr], Fc[gb], Fc[gt]);
         a.out.avg[c][id] = hi;
         a.out.lo[c][id] = lo;
         if (!isfinite(hi)) bad |= FLAG_NONFINITE;

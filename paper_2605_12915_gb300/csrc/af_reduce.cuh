@@ -19,6 +19,7 @@ struct RedArgs {
   const T* wc[4];
   int nx, ny;
   double gamma, h;
+  double rho_ref, p_ref, e_ref;  // storage offsets (see Gas)
   double* partial;  // [gridDim.x][RED_VALS]
 };
 
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_inv_partial(RedArgs<T> a) {
     double ub[4];
     for (int k = 0; k < 4; ++k) {
       ub[k] = (double)a.st.avg[k][id] + (COMP ? (double)a.st.lo[k][id] : 0.0);
+      ub[k] += k == 0 ? a.rho_ref : (k == 3 ? a.e_ref : 0.0);
       acc[k] += ub[k];
     }
     double ra = ub[0], ua = ub[1] / ra, va = ub[2] / ra;
@@ -52,6 +54,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_inv_partial(RedArgs<T> a) {
     double w[3][3][4];
     auto ld = [&](const T* const* pl, size_t q, double* o) {
       for (int k = 0; k < 4; ++k) o[k] = (double)pl[k][q];
+      o[0] += a.rho_ref;
+      o[3] += a.p_ref;
     };
     size_t q00 = id, q10 = (size_t)j * a.nx + ip, q01 = (size_t)jp * a.nx + i,
            q11 = (size_t)jp * a.nx + ip;

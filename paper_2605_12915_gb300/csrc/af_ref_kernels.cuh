@@ -25,7 +25,8 @@ struct StepArgs {
   T* gy[4];           // (dt/h) * time-integrated flux through horizontal edge (i,j)
   unsigned* flags;
   int nx, ny;
-  T h, dt, gamma, gm1, gm1inv;
+  T h, dt;
+  Gas<T> gas;
   int variant;        // 0 TAI, 1 RB
 };
 
@@ -71,18 +72,19 @@ __global__ void k_center(StepArgs<T> a) {
   const Prim<T> edges[4] = {P(2, i, j), P(2, i, jp), P(1, i, j), P(1, ip, j)};
   for (int n = 0; n < 4; ++n) {
     T u[4];
-    cons_from_prim(corners[n], a.gm1inv, u);
+    cons_from_stored(corners[n], a.gas, u);
     for (int k = 0; k < 4; ++k) c[k] += (ub[k] - u[k]) + lo[k];
-    cons_from_prim(edges[n], a.gm1inv, u);
+    cons_from_stored(edges[n], a.gas, u);
     for (int k = 0; k < 4; ++k) e[k] += (ub[k] - u[k]) + lo[k];
   }
   for (int k = 0; k < 4; ++k) uc[k] = (ub[k] + lo[k]) + (T(0.0625) * c[k] + T(0.25) * e[k]);
-  Prim<T> w = prim_from_cons(uc, a.gm1);
+  Prim<T> w = stored_from_cons(uc, a.gas);
   a.wc[0][id] = w.r;
   a.wc[1][id] = w.u;
   a.wc[2][id] = w.v;
   a.wc[3][id] = w.p;
-  raise_flag(a.flags, (w.r > T(0) && w.p > T(0)) ? 0u : FLAG_NONPHYSICAL);
+  raise_flag(a.flags, (a.gas.rho_ref + w.r > T(0) && a.gas.p_ref + w.p > T(0)) ? 0u
+                                                                             : FLAG_NONPHYSICAL);
 }
 
 // ---------------------------------------------------------------------------
@@ -135,9 +137,10 @@ __global__ void k_acoustic(StepArgs<T> a) {
   const int J = 2 * j + ((FAM == 1 || FAM == 3) ? 1 : 0);
   Prim<T> wk = L.at(I, J);
   unsigned bad = 0;
-  if (!(wk.r > T(0) && wk.p > T(0))) bad |= FLAG_NONPHYSICAL;
-  T c = sqrt(a.gamma * wk.p / wk.r);
-  T Z = wk.r * c, Zinv = T(1) / Z;
+  const T rk = a.gas.rho_ref + wk.r, pk = a.gas.p_ref + wk.p;
+  if (!(rk > T(0) && pk > T(0))) bad |= FLAG_NONPHYSICAL;
+  T c = sqrt(a.gas.gamma * pk / rk);
+  T Z = rk * c, Zinv = T(1) / Z;
   T r1 = c * a.dt / a.h;
   if (r1 > T(0.5)) bad |= FLAG_CFL;
   T Gp[3][4], Guv[3][4];
@@ -251,8 +254,9 @@ __global__ void k_points(StepArgs<T> a) {
       // transported increment evaluated at the foot; rho from dp / c_f^2
       T d[3];
       eval_d(D, fc, d);
-      if (!(wf.r > T(0) && wf.p > T(0))) bad |= FLAG_NONPHYSICAL;
-      nw.r = wf.r + d[2] * wf.r / (a.gamma * wf.p);
+      const T rf = a.gas.rho_ref + wf.r, pf = a.gas.p_ref + wf.p;
+      if (!(rf > T(0) && pf > T(0))) bad |= FLAG_NONPHYSICAL;
+      nw.r = wf.r + d[2] * rf / (a.gas.gamma * pf);
       nw.u = wf.u + d[0];
       nw.v = wf.v + d[1];
       nw.p = wf.p + d[2];
@@ -260,7 +264,7 @@ __global__ void k_points(StepArgs<T> a) {
       // additive update: S_ac(P) + S_adv(P) - W(P), acoustic rho closure at P
       T d[3];
       D.at(I, J, d);
-      nw.r = wf.r + d[2] * wp.r / (a.gamma * wp.p);
+      nw.r = wf.r + d[2] * (a.gas.rho_ref + wp.r) / (a.gas.gamma * (a.gas.p_ref + wp.p));
       nw.u = wf.u + d[0];
       nw.v = wf.v + d[1];
       nw.p = wf.p + d[2];
@@ -301,14 +305,14 @@ __global__ void k_flux(StepArgs<T> a) {
   for (int s = 0; s < 3; ++s) {
     T fa[4], fm[4], fb[4];
     // vertical edge x = x_i: V(i,j), E_v(i,j), V(i,j+1)
-    flux_x(load_pt<T>(lev[s][0], id), a.gm1inv, fa);
-    flux_x(load_pt<T>(lev[s][1], id), a.gm1inv, fm);
-    flux_x(load_pt<T>(lev[s][0], up), a.gm1inv, fb);
+    flux_x(load_pt<T>(lev[s][0], id), a.gas, fa);
+    flux_x(load_pt<T>(lev[s][1], id), a.gas, fm);
+    flux_x(load_pt<T>(lev[s][0], up), a.gas, fb);
     for (int k = 0; k < 4; ++k) F[k] = fma(wt[s], fa[k] + T(4) * fm[k] + fb[k], F[k]);
     // horizontal edge y = y_j: V(i,j), E_h(i,j), V(i+1,j)
-    flux_y(load_pt<T>(lev[s][0], id), a.gm1inv, fa);
-    flux_y(load_pt<T>(lev[s][2], id), a.gm1inv, fm);
-    flux_y(load_pt<T>(lev[s][0], rt), a.gm1inv, fb);
+    flux_y(load_pt<T>(lev[s][0], id), a.gas, fa);
+    flux_y(load_pt<T>(lev[s][2], id), a.gas, fm);
+    flux_y(load_pt<T>(lev[s][0], rt), a.gas, fb);
     for (int k = 0; k < 4; ++k) G[k] = fma(wt[s], fa[k] + T(4) * fm[k] + fb[k], G[k]);
   }
   const T lam = a.dt / (T(36) * a.h);
@@ -332,15 +336,8 @@ __global__ void k_average(StepArgs<T> a) {
   unsigned bad = 0;
   for (int k = 0; k < 4; ++k) {
     if constexpr (COMP) {
-      float hi = a.in.avg[k][id], lo = a.in.lo[k][id], e;
-      const float terms[4] = {a.fx[k][id], -a.fx[k][rt], a.gy[k][id], -a.gy[k][up]};
-      for (int t = 0; t < 4; ++t) {
-        two_sum(hi, terms[t], hi, e);
-        lo = __fadd_rn(lo, e);
-      }
-      float s = __fadd_rn(hi, lo);
-      lo = __fsub_rn(lo, __fsub_rn(s, hi));
-      hi = s;
+      float hi = a.in.avg[k][id], lo = a.in.lo[k][id];
+      comp_update(hi, lo, a.fx[k][id], a.fx[k][rt], a.gy[k][id], a.gy[k][up]);
       a.out.avg[k][id] = hi;
       a.out.lo[k][id] = lo;
       if (!isfinite(hi)) bad |= FLAG_NONFINITE;
