@@ -11,7 +11,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def _deps():
-    deps = [os.path.join(ROOT, "include", "af.h")]
+    deps = [os.path.join(ROOT, "include", "af.h"), os.path.abspath(__file__)]
     for f in os.listdir(CSRC):
         if f.endswith((".cu", ".cuh", ".h")):
             deps.append(os.path.join(CSRC, f))
@@ -32,7 +32,12 @@ def build(force=False, verbose=False, extra_flags=()):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in _deps()):
             return LIB
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+    # -fmad=false: no implicit multiply-add contraction.  Every value that two
+    # CTAs compute redundantly (tile-boundary points and edge fluxes) must round
+    # identically in every unrolled copy of the code, or conservation breaks;
+    # the hot loops use explicit fma() where fusion is wanted.
+    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
+           "-shared",
            "-o", LIB + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES], *extra_flags]
     if verbose:
         print(" ".join(cmd))

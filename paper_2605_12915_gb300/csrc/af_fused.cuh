@@ -109,7 +109,7 @@ __device__ __forceinline__ void eval_d_s(const float* LD, int base, float xi, fl
 template <int TX, int TY, int NT, bool COMP>
 __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
   using G = FusedGeom<TX, TY>;
-  constexpr int FW = G::FW, FH = G::FH, DW = G::DW, DH = G::DH, PW = G::PW, PH = G::PH;
+  constexpr int FW = G::FW, FH = G::FH, DW = G::DW, PW = G::PW, PH = G::PH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* LW = reinterpret_cast<float4*>(smem_raw);
   float* LD = reinterpret_cast<float*>(smem_raw + G::LW_BYTES);  // [2][LDS]: [DH][DW][3]
