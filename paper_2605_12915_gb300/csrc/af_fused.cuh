@@ -1,19 +1,23 @@
 // af_fused.cuh -- the whole RB-TAI / RB step (Sec. 6.1) in one FP32 kernel.
 //
 // Each CTA owns TX x TY cells.  Everything a step needs around them is staged
-// in shared memory on the half-cell lattice (see af_common.cuh):
-//   LW  time-n primitive values (rho,u,v,p) on the lattice covering cells
-//       [i0-2, i0+TX+3) x [j0-2, j0+TY+3); the centre nodes are filled by the
-//       Simpson inversion of this CTA (phase 1).
-//   LD  acoustic increments (du,dv,dp) for tau = dt/2 and dt on the lattice
-//       of every node of every cell a convective foot can reach (phase 2).
+// in shared memory, one plane per (node family, component), indexed by cell:
+//   W   time-n values (rho~, u, v, p~) of the vertex, x-edge, y-edge and
+//       centre families of cells [i0-2, i0+TX+4) x [j0-2, j0+TY+4); the centre
+//       family is filled by this CTA's Simpson inversion (phase 1).
+//   D   acoustic increments (du, dv, dp) of every family for tau = dt/2 and
+//       tau = dt, cells [i0-1, i0+TX+3): every node of every cell that a
+//       convective foot can reach (phase 2).
 // Phase 3 evaluates the two-Picard foot and the transported (or additive)
 // point update of the points of cells [i0, i0+TX] x [j0, j0+TY] for both
 // durations; the half-step values never leave the SM.  Phase 4 forms the
 // space-time Simpson edge fluxes and updates the owned cell averages.
-// A convective foot may lie up to one cell from its point in each direction
-// (displacements are clamped there and flagged, so shared-memory accesses stay
-// in bounds whatever the data).
+//
+// Planes of one family are rows of consecutive cells, so a warp working on 32
+// consecutive cells touches 32 consecutive words: no bank conflicts, and
+// stencil offsets become load immediates.  A convective foot may lie up to one
+// cell from its point in each direction; displacements are clamped there and
+// flagged, so every shared-memory access stays in bounds whatever the data.
 #pragma once
 
 #include "af_common.cuh"
@@ -24,195 +28,189 @@ namespace af {
 template <int TX_, int TY_>
 struct FusedGeom {
   static constexpr int TX = TX_, TY = TY_;
-  static constexpr int FW = 2 * TX + 11, FH = 2 * TY + 11;  // LW: fine [2i0-4, 2i0+2TX+6]
-  static constexpr int DW = 2 * TX + 7, DH = 2 * TY + 7;    // LD: fine [2i0-2, 2i0+2TX+4]
-  static constexpr int PW = TX + 1, PH = TY + 1;            // point cells [i0, i0+TX]
-  static constexpr int CW = TX + 6, CH = TY + 6;            // loaded cells [i0-2, i0+TX+4)
-  static constexpr int NW = TX + 5, NH = TY + 5;            // centre cells [i0-2, i0+TX+3)
-  static constexpr int NPTS = 3 * PW * PH;                 // points of one duration
-  static constexpr int LDS = (3 * DW * DH + 3) / 4 * 4;     // floats per duration in LD
-  static constexpr size_t LW_BYTES = sizeof(float4) * FW * FH;
-  static constexpr size_t LD_BYTES = sizeof(float) * 2 * LDS;
-  static constexpr size_t FL_BYTES = sizeof(float) * 4 * (PW * TY + TX * PH);
-  static constexpr size_t SMEM = LW_BYTES + LD_BYTES;
-  static_assert(FL_BYTES <= LW_BYTES, "fluxes alias the LW region");
-  static_assert(4 * NPTS <= LDS, "the points of one duration alias its increments");
+  static constexpr int CW = TX + 6, CH = TY + 6;    // W cells [i0-2, i0+TX+4)
+  static constexpr int DCW = TX + 4, DCH = TY + 4;  // D cells [i0-1, i0+TX+3)
+  static constexpr int PW = TX + 1, PH = TY + 1;    // point cells [i0, i0+TX]
+  static constexpr int WPL = CW * CH;               // floats per W plane
+  static constexpr int DPL = DCW * DCH;             // floats per D plane
+  static constexpr int PPL = PW * PH;               // floats per point plane
+  static constexpr int NPTS = 3 * PPL;              // points of one duration
+  static constexpr int NVE = PW * TY, NHE = TX * PH, NE = NVE + NHE;  // edges
+  static constexpr size_t W_BYTES = sizeof(float) * 16 * WPL;
+  static constexpr size_t D_BYTES = sizeof(float) * 24 * DPL;
+  static constexpr size_t SMEM = W_BYTES + D_BYTES;
+  static_assert(4 * NE <= 16 * WPL, "fluxes alias W");
+  static_assert(PPL <= DPL, "points of one duration alias its increments");
 };
 
-struct LoadSmem {
-  const float4* LW;
-  int base;  // index of the node itself
-  int fw;
+// Plane of W for (family f, component k): W + (4 f + k) WPL, k = rho~, u, v, p~.
+// Plane of D for (duration s, family f, component k): D + ((4 s + f) 3 + k) DPL,
+// k = du, dv, dp.  After phase 3 the points of duration s, plane (family f,
+// component k), live at D + 12 s DPL + (4 f + k) PPL.
+
+// Loader for the generated stencils: node of family F at W cell index `cell`;
+// a lattice offset (dx, dy) in half cells resolves at compile time to a family
+// plane and a cell offset.
+template <int F, int CW, int WPL>
+struct LoadW {
+  const float* W;
+  int cell;
   __device__ __forceinline__ PUV<float> operator()(int dx, int dy) const {
-    float4 w = LW[base + dy * fw + dx];
-    PUV<float> o = {w.w, w.y, w.z};
+    const int ax = ((F == 2 || F == 3) ? 1 : 0) + dx, by = ((F == 1 || F == 3) ? 1 : 0) + dy;
+    const int fam = (ax & 1) ? ((by & 1) ? 3 : 2) : ((by & 1) ? 1 : 0);
+    const float* base = W + 4 * fam * WPL + cell + (by >> 1) * CW + (ax >> 1);
+    PUV<float> o = {base[3 * WPL], base[WPL], base[2 * WPL]};
     return o;
   }
 };
 
-__device__ __forceinline__ Prim<float> as_prim(float4 w) {
-  Prim<float> p = {w.x, w.y, w.z, w.w};
-  return p;
-}
-
 __device__ __forceinline__ float clamp1(float d) { return fmaxf(fminf(d, 1.0f), -1.0f); }
 
-// Q2 evaluation of the four primitives from LW in the cell whose lower-left
-// lattice node is `base`.
-template <int FW>
-__device__ __forceinline__ Prim<float> eval_w_s(const float4* LW, int base, float xi,
-                                                float eta) {
-  float lx[3], ly[3];
-  lagrange3(xi, lx);
-  lagrange3(eta, ly);
-  Prim<float> s = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    Prim<float> row = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      float4 w = LW[base + b * FW + q];
-      row.r = fmaf(lx[q], w.x, row.r);
-      row.u = fmaf(lx[q], w.y, row.u);
-      row.v = fmaf(lx[q], w.z, row.v);
-      row.p = fmaf(lx[q], w.w, row.p);
-    }
-    s.r = fmaf(ly[b], row.r, s.r);
-    s.u = fmaf(ly[b], row.u, s.u);
-    s.v = fmaf(ly[b], row.v, s.v);
-    s.p = fmaf(ly[b], row.p, s.p);
-  }
-  return s;
-}
-
-template <int DW>
-__device__ __forceinline__ void eval_d_s(const float* LD, int base, float xi, float eta,
-                                         float out[3]) {
-  float lx[3], ly[3];
-  lagrange3(xi, lx);
-  lagrange3(eta, ly);
-  out[0] = out[1] = out[2] = 0.f;
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    float row[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float* d = LD + 3 * (base + b * DW + q);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) row[k] = fmaf(lx[q], d[k], row[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) out[k] = fmaf(ly[b], row[k], out[k]);
-  }
+// sum_ab l_a(xi) l_b(eta) f_ab over the nine nodes of the cell at index c of a
+// set of family planes (V, E_v, E_h, C) with row stride R.
+template <int R>
+__device__ __forceinline__ float q2_eval(const float* pV, const float* pEv, const float* pEh,
+                                         const float* pC, int c, const float lx[3],
+                                         const float ly[3]) {
+  const float r0 = fmaf(lx[0], pV[c], fmaf(lx[1], pEh[c], lx[2] * pV[c + 1]));
+  const float r1 = fmaf(lx[0], pEv[c], fmaf(lx[1], pC[c], lx[2] * pEv[c + 1]));
+  const float r2 = fmaf(lx[0], pV[c + R], fmaf(lx[1], pEh[c + R], lx[2] * pV[c + R + 1]));
+  return fmaf(ly[0], r0, fmaf(ly[1], r1, ly[2] * r2));
 }
 
 template <int TX, int TY, int NT, bool COMP>
 __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
   using G = FusedGeom<TX, TY>;
-  constexpr int FW = G::FW, FH = G::FH, DW = G::DW, PW = G::PW, PH = G::PH;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* LW = reinterpret_cast<float4*>(smem_raw);
-  float* LD = reinterpret_cast<float*>(smem_raw + G::LW_BYTES);  // [2][LDS]: [DH][DW][3]
-  // after phase 3 the points of duration s overwrite LD[s]: PT(s) = [3][PH][PW] float4
-  auto PT = [&](int s) { return reinterpret_cast<float4*>(LD + s * G::LDS); };
-  float* FLX = reinterpret_cast<float*>(smem_raw);                 // fluxes (after LW)
+  constexpr int CW = G::CW, CH = G::CH, DCW = G::DCW, PW = G::PW;
+  constexpr int WPL = G::WPL, DPL = G::DPL, PPL = G::PPL;
+  extern __shared__ __align__(16) float smem[];
+  float* W = smem;
+  float* D = smem + 16 * WPL;
+  float* FLX = smem;  // fluxes overwrite W in phase 4
 
   const int nx = a.nx, ny = a.ny;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const Gas<float> gas = a.gas;
   unsigned bad = 0;
 
   // ---- phase 0: point values of cells [i0-2, i0+TX+4) x [j0-2, j0+TY+4) ------
-  for (int t = threadIdx.x; t < G::CW * G::CH; t += NT) {
-    const int cx = t % G::CW, cy = t / G::CW;
-    const size_t id = (size_t)wrapi(j0 - 2 + cy, ny) * nx + wrapi(i0 - 2 + cx, nx);
-    const int lx = 2 * cx, ly = 2 * cy;
-    if (ly < FH) {
-      if (lx < FW)
-        LW[ly * FW + lx] = make_float4(__ldg(a.in.pt[0][0] + id), __ldg(a.in.pt[0][1] + id),
-                                       __ldg(a.in.pt[0][2] + id), __ldg(a.in.pt[0][3] + id));
-      if (lx + 1 < FW)
-        LW[ly * FW + lx + 1] = make_float4(__ldg(a.in.pt[2][0] + id), __ldg(a.in.pt[2][1] + id),
-                                           __ldg(a.in.pt[2][2] + id), __ldg(a.in.pt[2][3] + id));
+  {
+    const bool interior = i0 >= 2 && j0 >= 2 && i0 + CW - 2 <= nx && j0 + CH - 2 <= ny;
+    for (int t = threadIdx.x; t < CW * CH; t += NT) {
+      const int cx = t % CW, cy = t / CW;
+      int gi = i0 - 2 + cx, gj = j0 - 2 + cy;
+      if (!interior) {
+        gi = wrapi(gi, nx);
+        gj = wrapi(gj, ny);
+      }
+      const size_t id = (size_t)gj * nx + gi;
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) W[(4 * f + k) * WPL + t] = __ldg(a.in.pt[f][k] + id);
     }
-    if (ly + 1 < FH && lx < FW)
-      LW[(ly + 1) * FW + lx] = make_float4(__ldg(a.in.pt[1][0] + id), __ldg(a.in.pt[1][1] + id),
-                                           __ldg(a.in.pt[1][2] + id), __ldg(a.in.pt[1][3] + id));
   }
   __syncthreads();
 
   // ---- phase 1: centre recovery of cells [i0-2, i0+TX+3) (Eq. center-node) ----
-  for (int t = threadIdx.x; t < G::NW * G::NH; t += NT) {
-    const int cx = t % G::NW, cy = t / G::NW;
+  // deviation form U_c = Ubar + 1/16 sum_corners (Ubar - U_V) + 1/4 sum_edges (Ubar - U_E)
+  for (int t = threadIdx.x; t < (CW - 1) * (CH - 1); t += NT) {
+    const int cx = t % (CW - 1), cy = t / (CW - 1);
+    const int c = cy * CW + cx;
     const size_t id = (size_t)wrapi(j0 - 2 + cy, ny) * nx + wrapi(i0 - 2 + cx, nx);
-    float ub[4], lo[4], c[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f}, uc[4];
+    float ub[4], lo[4], sc[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f}, uc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       ub[k] = __ldg(a.in.avg[k] + id);
       lo[k] = COMP ? __ldg(a.in.lo[k] + id) : 0.f;
     }
-    const int b = (2 * cy) * FW + 2 * cx;  // lower-left lattice node of the cell
-    const int cidx[4] = {b, b + 2, b + 2 * FW, b + 2 * FW + 2};
-    const int eidx[4] = {b + 1, b + 2 * FW + 1, b + FW, b + FW + 2};
+    auto node = [&](int fam, int idx) {
+      Prim<float> w = {W[(4 * fam) * WPL + idx], W[(4 * fam + 1) * WPL + idx],
+                       W[(4 * fam + 2) * WPL + idx], W[(4 * fam + 3) * WPL + idx]};
+      return w;
+    };
+    const Prim<float> corners[4] = {node(0, c), node(0, c + 1), node(0, c + CW),
+                                    node(0, c + CW + 1)};
+    const Prim<float> edges[4] = {node(2, c), node(2, c + CW), node(1, c), node(1, c + 1)};
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
       float u[4];
-      cons_from_stored(as_prim(LW[cidx[n]]), a.gas, u);
+      cons_from_stored(corners[n], gas, u);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) c[k] += (ub[k] - u[k]) + lo[k];
-      cons_from_stored(as_prim(LW[eidx[n]]), a.gas, u);
+      for (int k = 0; k < 4; ++k) sc[k] += (ub[k] - u[k]) + lo[k];
+      cons_from_stored(edges[n], gas, u);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) e[k] += (ub[k] - u[k]) + lo[k];
+      for (int k = 0; k < 4; ++k) se[k] += (ub[k] - u[k]) + lo[k];
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) uc[k] = (ub[k] + lo[k]) + (0.0625f * c[k] + 0.25f * e[k]);
-    Prim<float> w = stored_from_cons(uc, a.gas);
-    if (!(a.gas.rho_ref + w.r > 0.f && a.gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
-    LW[b + FW + 1] = make_float4(w.r, w.u, w.v, w.p);
+    for (int k = 0; k < 4; ++k) uc[k] = (ub[k] + lo[k]) + (0.0625f * sc[k] + 0.25f * se[k]);
+    const Prim<float> w = stored_from_cons(uc, gas);
+    if (!(gas.rho_ref + w.r > 0.f && gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
+    W[12 * WPL + c] = w.r;
+    W[13 * WPL + c] = w.u;
+    W[14 * WPL + c] = w.v;
+    W[15 * WPL + c] = w.p;
   }
   __syncthreads();
 
-  // ---- phase 2: acoustic increments on LD (Sec. 6.1 step 1) -------------------
+  // ---- phase 2: acoustic increments (Sec. 6.1 step 1) -------------------------
+  // D cells: V [0,TX+4)x[0,TY+4), E_v [0,TX+4)x[0,TY+3), E_h [0,TX+3)x[0,TY+4),
+  // C [0,TX+3)x[0,TY+3); D cell (dx, dy) is W cell (dx+1, dy+1).
   {
     constexpr int nV = (TX + 4) * (TY + 4), nEv = (TX + 4) * (TY + 3),
                   nEh = (TX + 3) * (TY + 4), nC = (TX + 3) * (TY + 3);
+    const float dth = a.dt / a.h;
     for (int t = threadIdx.x; t < nV + nEv + nEh + nC; t += NT) {
       int fam, dx, dy;
       if (t < nV) {
-        fam = 0; dx = 2 * (t % (TX + 4)); dy = 2 * (t / (TX + 4));
+        fam = 0; dx = t % (TX + 4); dy = t / (TX + 4);
       } else if (t < nV + nEv) {
-        int u = t - nV; fam = 1; dx = 2 * (u % (TX + 4)); dy = 2 * (u / (TX + 4)) + 1;
+        fam = 1; dx = (t - nV) % (TX + 4); dy = (t - nV) / (TX + 4);
       } else if (t < nV + nEv + nEh) {
-        int u = t - nV - nEv; fam = 2; dx = 2 * (u % (TX + 3)) + 1; dy = 2 * (u / (TX + 3));
+        fam = 2; dx = (t - nV - nEv) % (TX + 3); dy = (t - nV - nEv) / (TX + 3);
       } else {
-        int u = t - nV - nEv - nEh; fam = 3; dx = 2 * (u % (TX + 3)) + 1; dy = 2 * (u / (TX + 3)) + 1;
+        fam = 3; dx = (t - nV - nEv - nEh) % (TX + 3); dy = (t - nV - nEv - nEh) / (TX + 3);
       }
-      const int node = (dy + 2) * FW + (dx + 2);
-      const float4 wk4 = LW[node];
-      const float rk = a.gas.rho_ref + wk4.x, pk = a.gas.p_ref + wk4.w;
+      const int wc = (dy + 1) * CW + (dx + 1), dc = dy * DCW + dx;
+      const float* Wf = W + 4 * fam * WPL;
+      const float rk = gas.rho_ref + Wf[wc], uk = Wf[WPL + wc], vk = Wf[2 * WPL + wc];
+      const float pkt = Wf[3 * WPL + wc], pk = gas.p_ref + pkt;
       if (!(rk > 0.f && pk > 0.f)) bad |= FLAG_NONPHYSICAL;
-      const float c = sqrtf(a.gas.gamma * pk / rk);
+      const float c = sqrtf(gas.gamma * pk / rk);
       const float Z = rk * c, Zinv = 1.f / Z;
-      const float r1 = c * a.dt / a.h;
+      const float r1 = c * dth;
       if (r1 > 0.5f) bad |= FLAG_CFL;
       float Gp[3][4], Guv[3][4];
-      LoadSmem ld = {LW, node, FW};
-      if (fam == 0) af_sac_V<float>(ld, wk4.w, wk4.y, wk4.z, Gp, Guv);
-      else if (fam == 1) af_sac_EV<float>(ld, wk4.w, wk4.y, wk4.z, Gp, Guv);
-      else if (fam == 2) af_sac_EH<float>(ld, wk4.w, wk4.y, wk4.z, Gp, Guv);
-      else af_sac_C<float>(ld, wk4.w, wk4.y, wk4.z, Gp, Guv);
+      if (fam == 0) {
+        LoadW<0, CW, WPL> ld = {W, wc};
+        af_sac_V<float>(ld, pkt, uk, vk, Gp, Guv);
+      } else if (fam == 1) {
+        LoadW<1, CW, WPL> ld = {W, wc};
+        af_sac_EV<float>(ld, pkt, uk, vk, Gp, Guv);
+      } else if (fam == 2) {
+        LoadW<2, CW, WPL> ld = {W, wc};
+        af_sac_EH<float>(ld, pkt, uk, vk, Gp, Guv);
+      } else {
+        LoadW<3, CW, WPL> ld = {W, wc};
+        af_sac_C<float>(ld, pkt, uk, vk, Gp, Guv);
+      }
       float d[3];
-      float* dst = LD + 3 * (dy * DW + dx);
+      float* D0 = D + fam * 3 * DPL + dc;
+      float* D1 = D + (4 + fam) * 3 * DPL + dc;
       increments_at(Gp, Guv, Z, Zinv, 0.5f * r1, d);
-      dst[0] = d[0]; dst[1] = d[1]; dst[2] = d[2];
+      D0[0] = d[0];
+      D0[DPL] = d[1];
+      D0[2 * DPL] = d[2];
       increments_at(Gp, Guv, Z, Zinv, r1, d);
-      dst += G::LDS;
-      dst[0] = d[0]; dst[1] = d[1]; dst[2] = d[2];
+      D1[0] = d[0];
+      D1[DPL] = d[1];
+      D1[2 * DPL] = d[2];
     }
   }
   __syncthreads();
 
   // ---- phase 3: point updates of cells [i0, i0+TX] x [j0, j0+TY] -------------
-  // duration by duration: the results of duration s replace LD[s] once every
+  // duration by duration; the points of duration s replace D(s) once every
   // thread is done reading it.
   constexpr int NPTS = G::NPTS;
   constexpr int PER = (NPTS + NT - 1) / NT;
@@ -220,53 +218,64 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
 #pragma unroll 1
   for (int s = 0; s < 2; ++s) {
     const float th = s == 0 ? 0.5f * th_full : th_full;
-    const float* LDs = LD + s * G::LDS;
+    const float* Ds = D + s * 12 * DPL;
     float4 res[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int t = threadIdx.x + k * NT;
       if (t >= NPTS) break;
-      const int fam = t / (PW * PH), rem = t % (PW * PH);
+      const int fam = t / PPL, rem = t - fam * PPL;
       const int px = rem % PW, py = rem / PW;
       const int ox = fam == 2 ? 1 : 0, oy = fam == 1 ? 1 : 0;
-      const int lxp = 2 * px + 4 + ox, lyp = 2 * py + 4 + oy;  // LW coordinates of P
-      const float4 wp = LW[lyp * FW + lxp];
+      const int wcP = (py + 2) * CW + (px + 2);  // W cell of the point's cell
+      const float* Wf = W + 4 * fam * WPL;
+      const float rp = Wf[wcP], up = Wf[WPL + wcP], vp = Wf[2 * WPL + wcP],
+                  pp = Wf[3 * WPL + wcP];
       // first Picard stage from the point's own velocity (Eq. adv-footpoint)
-      float d1x = -th * wp.y, d1y = -th * wp.z;
+      const float d1x = -th * up, d1y = -th * vp;
       if (!(fabsf(d1x) <= 1.f && fabsf(d1y) <= 1.f)) bad |= FLAG_REACH;
-      d1x = clamp1(d1x);
-      d1y = clamp1(d1y);
-      float fx = 0.5f * ox + d1x, fy = 0.5f * oy + d1y;
+      float fx = 0.5f * ox + clamp1(d1x), fy = 0.5f * oy + clamp1(d1y);
       float flx = floorf(fx), fly = floorf(fy);
-      const int cb = (lyp - oy + 2 * (int)fly) * FW + (lxp - ox + 2 * (int)flx);
-      const Prim<float> w1 = eval_w_s<FW>(LW, cb, 2.f * (fx - flx) - 1.f, 2.f * (fy - fly) - 1.f);
+      float lx[3], ly[3];
+      lagrange3(2.f * (fx - flx) - 1.f, lx);
+      lagrange3(2.f * (fy - fly) - 1.f, ly);
+      int c = wcP + (int)fly * CW + (int)flx;
+      const float u1 = q2_eval<CW>(W + 1 * WPL, W + 5 * WPL, W + 9 * WPL, W + 13 * WPL, c, lx, ly);
+      const float v1 = q2_eval<CW>(W + 2 * WPL, W + 6 * WPL, W + 10 * WPL, W + 14 * WPL, c, lx, ly);
       // the foot
-      float dfx = -th * w1.u, dfy = -th * w1.v;
+      const float dfx = -th * u1, dfy = -th * v1;
       if (!(fabsf(dfx) <= 1.f && fabsf(dfy) <= 1.f)) bad |= FLAG_REACH;
-      dfx = clamp1(dfx);
-      dfy = clamp1(dfy);
-      fx = 0.5f * ox + dfx;
-      fy = 0.5f * oy + dfy;
+      fx = 0.5f * ox + clamp1(dfx);
+      fy = 0.5f * oy + clamp1(dfy);
       flx = floorf(fx);
       fly = floorf(fy);
-      const float xi = 2.f * (fx - flx) - 1.f, eta = 2.f * (fy - fly) - 1.f;
-      const int fcx = lxp - ox + 2 * (int)flx, fcy = lyp - oy + 2 * (int)fly;  // LW coords
-      const Prim<float> wf = eval_w_s<FW>(LW, fcy * FW + fcx, xi, eta);
+      lagrange3(2.f * (fx - flx) - 1.f, lx);
+      lagrange3(2.f * (fy - fly) - 1.f, ly);
+      const int ix = (int)flx, iy = (int)fly;
+      c = wcP + iy * CW + ix;
+      Prim<float> wf;
+      wf.r = q2_eval<CW>(W + 0 * WPL, W + 4 * WPL, W + 8 * WPL, W + 12 * WPL, c, lx, ly);
+      wf.u = q2_eval<CW>(W + 1 * WPL, W + 5 * WPL, W + 9 * WPL, W + 13 * WPL, c, lx, ly);
+      wf.v = q2_eval<CW>(W + 2 * WPL, W + 6 * WPL, W + 10 * WPL, W + 14 * WPL, c, lx, ly);
+      wf.p = q2_eval<CW>(W + 3 * WPL, W + 7 * WPL, W + 11 * WPL, W + 15 * WPL, c, lx, ly);
       float d[3];
       Prim<float> nw;
       if (a.variant == 0) {
-        // transported increment at the foot, rho from dp / c_f^2 (Sec. 6.1 step 4)
-        eval_d_s<DW>(LDs, (fcy - 2) * DW + (fcx - 2), xi, eta, d);
-        const float rf = a.gas.rho_ref + wf.r, pf = a.gas.p_ref + wf.p;
+        // transported increment at the foot; rho from dp / c_f^2 (Sec. 6.1 step 4)
+        const int dcf = (py + 1 + iy) * DCW + (px + 1 + ix);  // D cell of the foot cell
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          d[q] = q2_eval<DCW>(Ds + (0 * 3 + q) * DPL, Ds + (1 * 3 + q) * DPL,
+                              Ds + (2 * 3 + q) * DPL, Ds + (3 * 3 + q) * DPL, dcf, lx, ly);
+        const float rf = gas.rho_ref + wf.r, pf = gas.p_ref + wf.p;
         if (!(rf > 0.f && pf > 0.f)) bad |= FLAG_NONPHYSICAL;
-        nw.r = wf.r + d[2] * rf / (a.gas.gamma * pf);
+        nw.r = wf.r + d[2] * rf / (gas.gamma * pf);
       } else {
         // additive update (Eq. barsukow-additive), acoustic rho closure at P
-        const float* dp = LDs + 3 * ((lyp - 2) * DW + (lxp - 2));
-        d[0] = dp[0];
-        d[1] = dp[1];
-        d[2] = dp[2];
-        nw.r = wf.r + d[2] * (a.gas.rho_ref + wp.x) / (a.gas.gamma * (a.gas.p_ref + wp.w));
+        const int dcp = (py + 1) * DCW + (px + 1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) d[q] = Ds[(fam * 3 + q) * DPL + dcp];
+        nw.r = wf.r + d[2] * (gas.rho_ref + rp) / (gas.gamma * (gas.p_ref + pp));
       }
       nw.u = wf.u + d[0];
       nw.v = wf.v + d[1];
@@ -284,21 +293,26 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
         a.out.pt[fam][3][id] = nw.p;
       }
     }
-    __syncthreads();  // LD[s] is dead from here
-    float4* P = PT(s);
+    __syncthreads();  // D(s) is dead from here
+    float* P = D + s * 12 * DPL;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int t = threadIdx.x + k * NT;
       if (t >= NPTS) break;
-      P[t] = res[k];
+      const int fam = t / PPL, rem = t - fam * PPL;
+      float* q = P + fam * 4 * PPL + rem;
+      q[0] = res[k].x;
+      q[PPL] = res[k].y;
+      q[2 * PPL] = res[k].z;
+      q[3 * PPL] = res[k].w;
     }
   }
   __syncthreads();
 
   // ---- phase 4: space-time Simpson fluxes (Sec. 3.1) and average update -------
   // vertical edges (i0+ex, j0+ey), ex in [0, TX], ey in [0, TY); horizontal edges
-  // ex in [0, TX), ey in [0, TY].  Computed into registers, then stored over LW.
-  constexpr int NVE = PW * TY, NHE = TX * PH, NE = NVE + NHE;
+  // ex in [0, TX), ey in [0, TY].  Computed into registers, then stored over W.
+  constexpr int NVE = G::NVE, NE = G::NE;
   constexpr int PERE = (NE + NT - 1) / NT;
   float flux[PERE][4];
   const float lam = a.dt / (36.f * a.h);
@@ -309,43 +323,50 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
     const bool vert = t < NVE;
     const int u = vert ? t : t - NVE;
     const int ex = vert ? u % PW : u % TX, ey = vert ? u / PW : u / TX;
-    // time-n nodes from LW, half/full from PT: a = V(ex,ey), m = E_v or E_h, b = next V
-    const int la = (2 * ey + 4) * FW + (2 * ex + 4);
-    const int lm = vert ? la + FW : la + 1;
-    const int lb = vert ? la + 2 * FW : la + 2;
-    const int pa = ey * PW + ex;
-    const int pm = (vert ? 1 : 2) * PW * PH + pa;
-    const int pb = vert ? pa + PW : pa + 1;
+    const int fm = vert ? 1 : 2;              // E_v or E_h
+    const int wa = (ey + 2) * CW + (ex + 2);  // W cell of V(ex, ey)
+    const int wb = vert ? wa + CW : wa + 1;   // the edge's other vertex
+    const int pa = ey * PW + ex, pb = vert ? pa + PW : pa + 1;
     float F[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      Prim<float> wa, wm, wb;
+      Prim<float> xa, xm, xb;
       if (s == 0) {
-        wa = as_prim(LW[la]); wm = as_prim(LW[lm]); wb = as_prim(LW[lb]);
+        xa = {W[0 * WPL + wa], W[1 * WPL + wa], W[2 * WPL + wa], W[3 * WPL + wa]};
+        const float* Wm = W + 4 * fm * WPL;
+        xm = {Wm[0 * WPL + wa], Wm[1 * WPL + wa], Wm[2 * WPL + wa], Wm[3 * WPL + wa]};
+        xb = {W[0 * WPL + wb], W[1 * WPL + wb], W[2 * WPL + wb], W[3 * WPL + wb]};
       } else {
-        const float4* P = PT(s - 1);
-        wa = as_prim(P[pa]); wm = as_prim(P[pm]); wb = as_prim(P[pb]);
+        const float* P = D + (s - 1) * 12 * DPL;
+        xa = {P[0 * PPL + pa], P[1 * PPL + pa], P[2 * PPL + pa], P[3 * PPL + pa]};
+        const float* Pm = P + fm * 4 * PPL;
+        xm = {Pm[0 * PPL + pa], Pm[1 * PPL + pa], Pm[2 * PPL + pa], Pm[3 * PPL + pa]};
+        xb = {P[0 * PPL + pb], P[1 * PPL + pb], P[2 * PPL + pb], P[3 * PPL + pb]};
       }
-      float fa[4], fm[4], fb[4];
+      float fa[4], fmid[4], fb[4];
       if (vert) {
-        flux_x(wa, a.gas, fa); flux_x(wm, a.gas, fm); flux_x(wb, a.gas, fb);
+        flux_x(xa, gas, fa);
+        flux_x(xm, gas, fmid);
+        flux_x(xb, gas, fb);
       } else {
-        flux_y(wa, a.gas, fa); flux_y(wm, a.gas, fm); flux_y(wb, a.gas, fb);
+        flux_y(xa, gas, fa);
+        flux_y(xm, gas, fmid);
+        flux_y(xb, gas, fb);
       }
       const float wt = s == 1 ? 4.f : 1.f;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) F[c] = fmaf(wt, fa[c] + 4.f * fm[c] + fb[c], F[c]);
+      for (int q = 0; q < 4; ++q) F[q] = fmaf(wt, fa[q] + 4.f * fmid[q] + fb[q], F[q]);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) flux[k][c] = lam * F[c];
+    for (int q = 0; q < 4; ++q) flux[k][q] = lam * F[q];
   }
-  __syncthreads();  // LW is dead from here
+  __syncthreads();  // W is dead from here
 #pragma unroll
   for (int k = 0; k < PERE; ++k) {
     const int t = threadIdx.x + k * NT;
     if (t >= NE) break;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) FLX[c * NE + t] = flux[k][c];
+    for (int q = 0; q < 4; ++q) FLX[q * NE + t] = flux[k][q];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < TX * TY; t += NT) {
@@ -353,20 +374,20 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
     const int gi = i0 + cx, gj = j0 + cy;
     if (gi >= nx || gj >= ny) continue;
     const size_t id = (size_t)gj * nx + gi;
-    const int fl = cy * PW + cx, fr = fl + 1;            // vertical edges x_i, x_{i+1}
-    const int gb = NVE + cy * TX + cx, gt = gb + TX;     // horizontal edges y_j, y_{j+1}
+    const int fl = cy * PW + cx, fr = fl + 1;         // vertical edges x_i, x_{i+1}
+    const int gb = NVE + cy * TX + cx, gt = gb + TX;  // horizontal edges y_j, y_{j+1}
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float* Fc = FLX + c * NE;
+    for (int q = 0; q < 4; ++q) {
+      const float* Fq = FLX + q * NE;
       if (COMP) {
-        float hi = __ldg(a.in.avg[c] + id), lo = __ldg(a.in.lo[c] + id);
-        comp_update(hi, lo, Fc[fl], Fc[fr], Fc[gb], Fc[gt]);
-        a.out.avg[c][id] = hi;
-        a.out.lo[c][id] = lo;
+        float hi = __ldg(a.in.avg[q] + id), lo = __ldg(a.in.lo[q] + id);
+        comp_update(hi, lo, Fq[fl], Fq[fr], Fq[gb], Fq[gt]);
+        a.out.avg[q][id] = hi;
+        a.out.lo[q][id] = lo;
         if (!isfinite(hi)) bad |= FLAG_NONFINITE;
       } else {
-        const float v = __ldg(a.in.avg[c] + id) - (Fc[fr] - Fc[fl]) - (Fc[gt] - Fc[gb]);
-        a.out.avg[c][id] = v;
+        const float v = __ldg(a.in.avg[q] + id) - (Fq[fr] - Fq[fl]) - (Fq[gt] - Fq[gb]);
+        a.out.avg[q][id] = v;
         if (!isfinite(v)) bad |= FLAG_NONFINITE;
       }
     }
