@@ -129,6 +129,27 @@ void af_destroy(af_handle *h);
 /* Static text for a status code. */
 const char *af_status_string(af_status s);
 
+/* Largest grid, in cells (nx * ny), that af_step_noalloc accepts. */
+#define AF_NOALLOC_MAX_CELLS (128 * 128)
+
+/* One FP64 step that allocates nothing.  The paper has no counterpart: this
+ * serves callers that may not allocate device memory at all -- code running
+ * under a fixed, pre-reserved device-memory budget, or inside a host runtime
+ * that owns every allocation on the device.  The caller passes the state at
+ * t^n (`in`) and receives the state at t^n + dt (`out`), both FP64 device
+ * arrays in the layout above, on the current device, not overlapping.  The
+ * intermediate values live in one work area compiled into the library (a
+ * static device array of about 6.3 MB that every GPU loading the library holds
+ * until the process exits); no cudaMalloc, cudaFree or other allocating call
+ * is made.  The first call on a device looks up the work area's address on
+ * that device (make it before any stream capture).  Every call shares the one
+ * work area: calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller.  Synchronises `cuda_stream` and
+ * returns the step's error status; nx * ny > AF_NOALLOC_MAX_CELLS, or any
+ * other invalid argument, returns AF_ERR_ARG without touching the GPU. */
+af_status af_step_noalloc(const af_grid *g, double gamma, double dt, af_variant var,
+                          const af_state_f64 *in, const af_state_f64 *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
