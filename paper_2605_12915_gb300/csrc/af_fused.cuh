@@ -1,8 +1,8 @@
 // af_fused.cuh -- the whole RB-TAI / RB step (Sec. 6.1) in one FP32 kernel.
 //
 // Each CTA owns TX x TY cells.  Everything a step needs around them is staged
-// in shared memory, one plane per (node family, component), indexed by cell:
-//   W   time-n values (rho~, u, v, p~) of the vertex, x-edge, y-edge and
+// in shared memory, one plane per node family, indexed by cell:
+//   W   time-n values float4 (rho~, u, v, p~) of the vertex, x-edge, y-edge and
 //       centre families of cells [i0-2, i0+TX+4) x [j0-2, j0+TY+4); the centre
 //       family is filled by this CTA's Simpson inversion (phase 1).
 //   D   acoustic increments (du, dv, dp) of every family for tau = dt/2 and
@@ -14,8 +14,9 @@
 // space-time Simpson edge fluxes and updates the owned cell averages.
 //
 // Planes of one family are rows of consecutive cells, so a warp working on 32
-// consecutive cells touches 32 consecutive words: no bank conflicts, and
-// stencil offsets become load immediates.  A convective foot may lie up to one
+// consecutive cells touches consecutive addresses: no bank conflicts, and
+// stencil offsets become load immediates.  Phase 0 issues every global load of
+// the step at once (the averages wait in the increment region until phase 1).  A convective foot may lie up to one
 // cell from its point in each direction; displacements are clamped there and
 // flagged, so every shared-memory access stays in bounds whatever the data.
 #pragma once
@@ -31,43 +32,70 @@ struct FusedGeom {
   static constexpr int CW = TX + 6, CH = TY + 6;    // W cells [i0-2, i0+TX+4)
   static constexpr int DCW = TX + 4, DCH = TY + 4;  // D cells [i0-1, i0+TX+3)
   static constexpr int PW = TX + 1, PH = TY + 1;    // point cells [i0, i0+TX]
-  static constexpr int WPL = CW * CH;               // floats per W plane
+  static constexpr int WPL = CW * CH;               // nodes per W plane
   static constexpr int DPL = DCW * DCH;             // floats per D plane
-  static constexpr int PPL = PW * PH;               // floats per point plane
+  static constexpr int PPL = PW * PH;               // nodes per point plane
   static constexpr int NPTS = 3 * PPL;              // points of one duration
   static constexpr int NVE = PW * TY, NHE = TX * PH, NE = NVE + NHE;  // edges
-  static constexpr size_t W_BYTES = sizeof(float) * 16 * WPL;
-  static constexpr size_t D_BYTES = sizeof(float) * 24 * DPL;
-  static constexpr size_t SMEM = W_BYTES + D_BYTES;
-  static_assert(4 * NE <= 16 * WPL, "fluxes alias W");
-  static_assert(PPL <= DPL, "points of one duration alias its increments");
+  static constexpr size_t W_BYTES = sizeof(float4) * 4 * WPL;
+  static constexpr size_t DS_BYTES = sizeof(float) * 12 * DPL;  // one duration
+  static constexpr size_t SMEM = W_BYTES + 2 * DS_BYTES;
+  static_assert(4 * NE * sizeof(float) <= W_BYTES, "fluxes alias W");
+  static_assert(3 * PPL * sizeof(float4) <= DS_BYTES, "points of one duration alias its increments");
+  static_assert(8 * WPL * sizeof(float) <= 2 * DS_BYTES, "averages wait in the D region");
+  static_assert(W_BYTES % 16 == 0 && DS_BYTES % 16 == 0, "float4 alignment");
 };
 
-// Plane of W for (family f, component k): W + (4 f + k) WPL, k = rho~, u, v, p~.
-// Plane of D for (duration s, family f, component k): D + ((4 s + f) 3 + k) DPL,
-// k = du, dv, dp.  After phase 3 the points of duration s, plane (family f,
-// component k), live at D + 12 s DPL + (4 f + k) PPL.
+// W plane of family f: W + f WPL (float4 per node: rho~, u, v, p~).
+// D plane of (duration s, family f, component k): D + ((4 s + f) 3 + k) DPL,
+// k = du, dv, dp.  After phase 3 the points of duration s of family f live at
+// PT(s) + f PPL (float4), PT(s) = the start of D(s).  During phases 0-1 the
+// averages (and lo words) of the W cells occupy D as 8 planes of WPL floats.
 
 // Loader for the generated stencils: node of family F at W cell index `cell`;
 // a lattice offset (dx, dy) in half cells resolves at compile time to a family
 // plane and a cell offset.
 template <int F, int CW, int WPL>
 struct LoadW {
-  const float* W;
+  const float4* W;
   int cell;
   __device__ __forceinline__ PUV<float> operator()(int dx, int dy) const {
     const int ax = ((F == 2 || F == 3) ? 1 : 0) + dx, by = ((F == 1 || F == 3) ? 1 : 0) + dy;
     const int fam = (ax & 1) ? ((by & 1) ? 3 : 2) : ((by & 1) ? 1 : 0);
-    const float* base = W + 4 * fam * WPL + cell + (by >> 1) * CW + (ax >> 1);
-    PUV<float> o = {base[3 * WPL], base[WPL], base[2 * WPL]};
+    const float4 w = W[fam * WPL + cell + (by >> 1) * CW + (ax >> 1)];
+    PUV<float> o = {w.w, w.y, w.z};
     return o;
   }
 };
 
 __device__ __forceinline__ float clamp1(float d) { return fmaxf(fminf(d, 1.0f), -1.0f); }
 
+__device__ __forceinline__ Prim<float> prim4(float4 w) {
+  Prim<float> p = {w.x, w.y, w.z, w.w};
+  return p;
+}
+
+// The nine W nodes of the cell at index c, ordered [b][a] (eta row, xi column).
+template <int CW, int WPL>
+__device__ __forceinline__ void load_cell(const float4* W, int c, float4 n[9]) {
+  n[0] = W[c];                    // V(c)
+  n[1] = W[2 * WPL + c];          // E_h(c)
+  n[2] = W[c + 1];                // V(c+1)
+  n[3] = W[WPL + c];              // E_v(c)
+  n[4] = W[3 * WPL + c];          // C(c)
+  n[5] = W[WPL + c + 1];          // E_v(c+1)
+  n[6] = W[c + CW];               // V(c+row)
+  n[7] = W[2 * WPL + c + CW];     // E_h(c+row)
+  n[8] = W[c + CW + 1];           // V(c+row+1)
+}
+
+#define AF_Q2(n, f, lx, ly)                                                        \
+  fmaf((ly)[0], fmaf((lx)[0], (n)[0].f, fmaf((lx)[1], (n)[1].f, (lx)[2] * (n)[2].f)), \
+       fmaf((ly)[1], fmaf((lx)[0], (n)[3].f, fmaf((lx)[1], (n)[4].f, (lx)[2] * (n)[5].f)), \
+            (ly)[2] * fmaf((lx)[0], (n)[6].f, fmaf((lx)[1], (n)[7].f, (lx)[2] * (n)[8].f))))
+
 // sum_ab l_a(xi) l_b(eta) f_ab over the nine nodes of the cell at index c of a
-// set of family planes (V, E_v, E_h, C) with row stride R.
+// set of scalar family planes (V, E_v, E_h, C) with row stride R.
 template <int R>
 __device__ __forceinline__ float q2_eval(const float* pV, const float* pEv, const float* pEh,
                                          const float* pC, int c, const float lx[3],
@@ -78,36 +106,71 @@ __device__ __forceinline__ float q2_eval(const float* pV, const float* pEv, cons
   return fmaf(ly[0], r0, fmaf(ly[1], r1, ly[2] * r2));
 }
 
+// local coordinates of a point displaced by d (cells) from lattice offset o (0
+// or 1 half cell): cell offset (floor) and Lagrange weights.
+__device__ __forceinline__ int foot_axis(int o, float d, float l[3]) {
+  const float f = 0.5f * o + d;
+  const float fl = floorf(f);
+  lagrange3(2.f * (f - fl) - 1.f, l);
+  return (int)fl;
+}
+
 template <int TX, int TY, int NT, bool COMP>
 __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
   using G = FusedGeom<TX, TY>;
   constexpr int CW = G::CW, CH = G::CH, DCW = G::DCW, PW = G::PW;
   constexpr int WPL = G::WPL, DPL = G::DPL, PPL = G::PPL;
-  extern __shared__ __align__(16) float smem[];
-  float* W = smem;
-  float* D = smem + 16 * WPL;
-  float* FLX = smem;  // fluxes overwrite W in phase 4
+  extern __shared__ __align__(16) float4 smem4[];
+  float4* W = smem4;
+  float* D = reinterpret_cast<float*>(smem4 + 4 * WPL);
+  float* FLX = reinterpret_cast<float*>(smem4);  // fluxes overwrite W in phase 4
 
   const int nx = a.nx, ny = a.ny;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const Gas<float> gas = a.gas;
   unsigned bad = 0;
 
-  // ---- phase 0: point values of cells [i0-2, i0+TX+4) x [j0-2, j0+TY+4) ------
+  // ---- phase 0: every global load of the step, cells [i0-2, i0+TX+4)^2 ------
   {
+    constexpr int NLOAD = CW * CH;
+    constexpr int PER0 = (NLOAD + NT - 1) / NT;
     const bool interior = i0 >= 2 && j0 >= 2 && i0 + CW - 2 <= nx && j0 + CH - 2 <= ny;
-    for (int t = threadIdx.x; t < CW * CH; t += NT) {
-      const int cx = t % CW, cy = t / CW;
-      int gi = i0 - 2 + cx, gj = j0 - 2 + cy;
-      if (!interior) {
-        gi = wrapi(gi, nx);
-        gj = wrapi(gj, ny);
+    float4 pv[PER0][3];
+    float av[PER0][4], lv[PER0][4];
+#pragma unroll
+    for (int k = 0; k < PER0; ++k) {
+      const int t = threadIdx.x + k * NT;
+      if (t < NLOAD) {
+        const int cx = t % CW, cy = t / CW;
+        int gi = i0 - 2 + cx, gj = j0 - 2 + cy;
+        if (!interior) {
+          gi = wrapi(gi, nx);
+          gj = wrapi(gj, ny);
+        }
+        const size_t id = (size_t)gj * nx + gi;
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+          pv[k][f] = make_float4(__ldg(a.in.pt[f][0] + id), __ldg(a.in.pt[f][1] + id),
+                                 __ldg(a.in.pt[f][2] + id), __ldg(a.in.pt[f][3] + id));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          av[k][q] = __ldg(a.in.avg[q] + id);
+          lv[k][q] = COMP ? __ldg(a.in.lo[q] + id) : 0.f;
+        }
       }
-      const size_t id = (size_t)gj * nx + gi;
+    }
 #pragma unroll
-      for (int f = 0; f < 3; ++f)
+    for (int k = 0; k < PER0; ++k) {
+      const int t = threadIdx.x + k * NT;
+      if (t < NLOAD) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) W[(4 * f + k) * WPL + t] = __ldg(a.in.pt[f][k] + id);
+        for (int f = 0; f < 3; ++f) W[f * WPL + t] = pv[k][f];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          D[q * WPL + t] = av[k][q];
+          if (COMP) D[(4 + q) * WPL + t] = lv[k][q];
+        }
+      }
     }
   }
   __syncthreads();
@@ -117,28 +180,21 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
   for (int t = threadIdx.x; t < (CW - 1) * (CH - 1); t += NT) {
     const int cx = t % (CW - 1), cy = t / (CW - 1);
     const int c = cy * CW + cx;
-    const size_t id = (size_t)wrapi(j0 - 2 + cy, ny) * nx + wrapi(i0 - 2 + cx, nx);
     float ub[4], lo[4], sc[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f}, uc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      ub[k] = __ldg(a.in.avg[k] + id);
-      lo[k] = COMP ? __ldg(a.in.lo[k] + id) : 0.f;
+      ub[k] = D[k * WPL + c];
+      lo[k] = COMP ? D[(4 + k) * WPL + c] : 0.f;
     }
-    auto node = [&](int fam, int idx) {
-      Prim<float> w = {W[(4 * fam) * WPL + idx], W[(4 * fam + 1) * WPL + idx],
-                       W[(4 * fam + 2) * WPL + idx], W[(4 * fam + 3) * WPL + idx]};
-      return w;
-    };
-    const Prim<float> corners[4] = {node(0, c), node(0, c + 1), node(0, c + CW),
-                                    node(0, c + CW + 1)};
-    const Prim<float> edges[4] = {node(2, c), node(2, c + CW), node(1, c), node(1, c + 1)};
+    const float4 corners[4] = {W[c], W[c + 1], W[c + CW], W[c + CW + 1]};
+    const float4 edges[4] = {W[2 * WPL + c], W[2 * WPL + c + CW], W[WPL + c], W[WPL + c + 1]};
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
       float u[4];
-      cons_from_stored(corners[n], gas, u);
+      cons_from_stored(prim4(corners[n]), gas, u);
 #pragma unroll
       for (int k = 0; k < 4; ++k) sc[k] += (ub[k] - u[k]) + lo[k];
-      cons_from_stored(edges[n], gas, u);
+      cons_from_stored(prim4(edges[n]), gas, u);
 #pragma unroll
       for (int k = 0; k < 4; ++k) se[k] += (ub[k] - u[k]) + lo[k];
     }
@@ -146,10 +202,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
     for (int k = 0; k < 4; ++k) uc[k] = (ub[k] + lo[k]) + (0.0625f * sc[k] + 0.25f * se[k]);
     const Prim<float> w = stored_from_cons(uc, gas);
     if (!(gas.rho_ref + w.r > 0.f && gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
-    W[12 * WPL + c] = w.r;
-    W[13 * WPL + c] = w.u;
-    W[14 * WPL + c] = w.v;
-    W[15 * WPL + c] = w.p;
+    W[3 * WPL + c] = make_float4(w.r, w.u, w.v, w.p);
   }
   __syncthreads();
 
@@ -172,9 +225,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
         fam = 3; dx = (t - nV - nEv - nEh) % (TX + 3); dy = (t - nV - nEv - nEh) / (TX + 3);
       }
       const int wc = (dy + 1) * CW + (dx + 1), dc = dy * DCW + dx;
-      const float* Wf = W + 4 * fam * WPL;
-      const float rk = gas.rho_ref + Wf[wc], uk = Wf[WPL + wc], vk = Wf[2 * WPL + wc];
-      const float pkt = Wf[3 * WPL + wc], pk = gas.p_ref + pkt;
+      const float4 wk = W[fam * WPL + wc];
+      const float rk = gas.rho_ref + wk.x, pk = gas.p_ref + wk.w;
       if (!(rk > 0.f && pk > 0.f)) bad |= FLAG_NONPHYSICAL;
       const float c = sqrtf(gas.gamma * pk / rk);
       const float Z = rk * c, Zinv = 1.f / Z;
@@ -183,16 +235,16 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
       float Gp[3][4], Guv[3][4];
       if (fam == 0) {
         LoadW<0, CW, WPL> ld = {W, wc};
-        af_sac_V<float>(ld, pkt, uk, vk, Gp, Guv);
+        af_sac_V<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
       } else if (fam == 1) {
         LoadW<1, CW, WPL> ld = {W, wc};
-        af_sac_EV<float>(ld, pkt, uk, vk, Gp, Guv);
+        af_sac_EV<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
       } else if (fam == 2) {
         LoadW<2, CW, WPL> ld = {W, wc};
-        af_sac_EH<float>(ld, pkt, uk, vk, Gp, Guv);
+        af_sac_EH<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
       } else {
         LoadW<3, CW, WPL> ld = {W, wc};
-        af_sac_C<float>(ld, pkt, uk, vk, Gp, Guv);
+        af_sac_C<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
       }
       float d[3];
       float* D0 = D + fam * 3 * DPL + dc;
@@ -211,7 +263,8 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
 
   // ---- phase 3: point updates of cells [i0, i0+TX] x [j0, j0+TY] -------------
   // duration by duration; the points of duration s replace D(s) once every
-  // thread is done reading it.
+  // thread is done reading it.  The nine nodes of the first Picard stage's
+  // cell are loaded once and reused for the foot when it lies in the same cell.
   constexpr int NPTS = G::NPTS;
   constexpr int PER = (NPTS + NT - 1) / NT;
   const float th_full = a.dt / a.h;
@@ -228,36 +281,28 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
       const int px = rem % PW, py = rem / PW;
       const int ox = fam == 2 ? 1 : 0, oy = fam == 1 ? 1 : 0;
       const int wcP = (py + 2) * CW + (px + 2);  // W cell of the point's cell
-      const float* Wf = W + 4 * fam * WPL;
-      const float rp = Wf[wcP], up = Wf[WPL + wcP], vp = Wf[2 * WPL + wcP],
-                  pp = Wf[3 * WPL + wcP];
+      const float4 wp = W[fam * WPL + wcP];
       // first Picard stage from the point's own velocity (Eq. adv-footpoint)
-      const float d1x = -th * up, d1y = -th * vp;
+      const float d1x = -th * wp.y, d1y = -th * wp.z;
       if (!(fabsf(d1x) <= 1.f && fabsf(d1y) <= 1.f)) bad |= FLAG_REACH;
-      float fx = 0.5f * ox + clamp1(d1x), fy = 0.5f * oy + clamp1(d1y);
-      float flx = floorf(fx), fly = floorf(fy);
       float lx[3], ly[3];
-      lagrange3(2.f * (fx - flx) - 1.f, lx);
-      lagrange3(2.f * (fy - fly) - 1.f, ly);
-      int c = wcP + (int)fly * CW + (int)flx;
-      const float u1 = q2_eval<CW>(W + 1 * WPL, W + 5 * WPL, W + 9 * WPL, W + 13 * WPL, c, lx, ly);
-      const float v1 = q2_eval<CW>(W + 2 * WPL, W + 6 * WPL, W + 10 * WPL, W + 14 * WPL, c, lx, ly);
+      int ix = foot_axis(ox, clamp1(d1x), lx), iy = foot_axis(oy, clamp1(d1y), ly);
+      const int c1 = wcP + iy * CW + ix;
+      float4 n[9];
+      load_cell<CW, WPL>(W, c1, n);
+      const float u1 = AF_Q2(n, y, lx, ly), v1 = AF_Q2(n, z, lx, ly);
       // the foot
       const float dfx = -th * u1, dfy = -th * v1;
       if (!(fabsf(dfx) <= 1.f && fabsf(dfy) <= 1.f)) bad |= FLAG_REACH;
-      fx = 0.5f * ox + clamp1(dfx);
-      fy = 0.5f * oy + clamp1(dfy);
-      flx = floorf(fx);
-      fly = floorf(fy);
-      lagrange3(2.f * (fx - flx) - 1.f, lx);
-      lagrange3(2.f * (fy - fly) - 1.f, ly);
-      const int ix = (int)flx, iy = (int)fly;
-      c = wcP + iy * CW + ix;
+      ix = foot_axis(ox, clamp1(dfx), lx);
+      iy = foot_axis(oy, clamp1(dfy), ly);
+      const int c2 = wcP + iy * CW + ix;
+      if (c2 != c1) load_cell<CW, WPL>(W, c2, n);
       Prim<float> wf;
-      wf.r = q2_eval<CW>(W + 0 * WPL, W + 4 * WPL, W + 8 * WPL, W + 12 * WPL, c, lx, ly);
-      wf.u = q2_eval<CW>(W + 1 * WPL, W + 5 * WPL, W + 9 * WPL, W + 13 * WPL, c, lx, ly);
-      wf.v = q2_eval<CW>(W + 2 * WPL, W + 6 * WPL, W + 10 * WPL, W + 14 * WPL, c, lx, ly);
-      wf.p = q2_eval<CW>(W + 3 * WPL, W + 7 * WPL, W + 11 * WPL, W + 15 * WPL, c, lx, ly);
+      wf.r = AF_Q2(n, x, lx, ly);
+      wf.u = AF_Q2(n, y, lx, ly);
+      wf.v = AF_Q2(n, z, lx, ly);
+      wf.p = AF_Q2(n, w, lx, ly);
       float d[3];
       Prim<float> nw;
       if (a.variant == 0) {
@@ -275,7 +320,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
         const int dcp = (py + 1) * DCW + (px + 1);
 #pragma unroll
         for (int q = 0; q < 3; ++q) d[q] = Ds[(fam * 3 + q) * DPL + dcp];
-        nw.r = wf.r + d[2] * (gas.rho_ref + rp) / (gas.gamma * (gas.p_ref + pp));
+        nw.r = wf.r + d[2] * (gas.rho_ref + wp.x) / (gas.gamma * (gas.p_ref + wp.w));
       }
       nw.u = wf.u + d[0];
       nw.v = wf.v + d[1];
@@ -294,17 +339,12 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
       }
     }
     __syncthreads();  // D(s) is dead from here
-    float* P = D + s * 12 * DPL;
+    float4* P = reinterpret_cast<float4*>(D + s * 12 * DPL);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int t = threadIdx.x + k * NT;
       if (t >= NPTS) break;
-      const int fam = t / PPL, rem = t - fam * PPL;
-      float* q = P + fam * 4 * PPL + rem;
-      q[0] = res[k].x;
-      q[PPL] = res[k].y;
-      q[2 * PPL] = res[k].z;
-      q[3 * PPL] = res[k].w;
+      P[t] = res[k];  // t = fam * PPL + rem
     }
   }
   __syncthreads();
@@ -332,16 +372,14 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
     for (int s = 0; s < 3; ++s) {
       Prim<float> xa, xm, xb;
       if (s == 0) {
-        xa = {W[0 * WPL + wa], W[1 * WPL + wa], W[2 * WPL + wa], W[3 * WPL + wa]};
-        const float* Wm = W + 4 * fm * WPL;
-        xm = {Wm[0 * WPL + wa], Wm[1 * WPL + wa], Wm[2 * WPL + wa], Wm[3 * WPL + wa]};
-        xb = {W[0 * WPL + wb], W[1 * WPL + wb], W[2 * WPL + wb], W[3 * WPL + wb]};
+        xa = prim4(W[wa]);
+        xm = prim4(W[fm * WPL + wa]);
+        xb = prim4(W[wb]);
       } else {
-        const float* P = D + (s - 1) * 12 * DPL;
-        xa = {P[0 * PPL + pa], P[1 * PPL + pa], P[2 * PPL + pa], P[3 * PPL + pa]};
-        const float* Pm = P + fm * 4 * PPL;
-        xm = {Pm[0 * PPL + pa], Pm[1 * PPL + pa], Pm[2 * PPL + pa], Pm[3 * PPL + pa]};
-        xb = {P[0 * PPL + pb], P[1 * PPL + pb], P[2 * PPL + pb], P[3 * PPL + pb]};
+        const float4* P = reinterpret_cast<const float4*>(D + (s - 1) * 12 * DPL);
+        xa = prim4(P[pa]);
+        xm = prim4(P[fm * PPL + pa]);
+        xb = prim4(P[pb]);
       }
       float fa[4], fmid[4], fb[4];
       if (vert) {
