@@ -131,44 +131,58 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
   unsigned bad = 0;
 
   // ---- phase 0: every global load of the step, cells [i0-2, i0+TX+4)^2 ------
+  // Interior tiles read 16-byte quads of cells [i0-4, i0+TX+4) per row (rows are
+  // 16-byte aligned when nx is a multiple of 4); tiles touching the periodic
+  // boundary read cell by cell with wrapped indices.
   {
-    constexpr int NLOAD = CW * CH;
-    constexpr int PER0 = (NLOAD + NT - 1) / NT;
-    const bool interior = i0 >= 2 && j0 >= 2 && i0 + CW - 2 <= nx && j0 + CH - 2 <= ny;
-    float4 pv[PER0][3];
-    float av[PER0][4], lv[PER0][4];
-#pragma unroll
-    for (int k = 0; k < PER0; ++k) {
-      const int t = threadIdx.x + k * NT;
-      if (t < NLOAD) {
-        const int cx = t % CW, cy = t / CW;
-        int gi = i0 - 2 + cx, gj = j0 - 2 + cy;
-        if (!interior) {
-          gi = wrapi(gi, nx);
-          gj = wrapi(gj, ny);
-        }
-        const size_t id = (size_t)gj * nx + gi;
+    const bool interior = i0 >= 4 && j0 >= 2 && i0 + TX + 4 <= nx && j0 + CH - 2 <= ny &&
+                          (nx & 3) == 0;
+    if (interior) {
+      constexpr int QW = (TX + 8) / 4;  // quads per row
+      static_assert(TX % 4 == 0, "quad loads need TX % 4 == 0");
+      for (int t = threadIdx.x; t < QW * CH; t += NT) {
+        const int m = t % QW, cy = t / QW;
+        const size_t id = (size_t)(j0 - 2 + cy) * nx + (i0 - 4 + 4 * m);
+        float4 pv[3][4], av[4], lv[4];
 #pragma unroll
         for (int f = 0; f < 3; ++f)
-          pv[k][f] = make_float4(__ldg(a.in.pt[f][0] + id), __ldg(a.in.pt[f][1] + id),
-                                 __ldg(a.in.pt[f][2] + id), __ldg(a.in.pt[f][3] + id));
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            pv[f][k] = __ldg(reinterpret_cast<const float4*>(a.in.pt[f][k] + id));
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          av[k][q] = __ldg(a.in.avg[q] + id);
-          lv[k][q] = COMP ? __ldg(a.in.lo[q] + id) : 0.f;
+          av[q] = __ldg(reinterpret_cast<const float4*>(a.in.avg[q] + id));
+          lv[q] = COMP ? __ldg(reinterpret_cast<const float4*>(a.in.lo[q] + id))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int cx = 4 * m + e - 2;  // W column of this cell
+          if (cx < 0 || cx >= CW) continue;
+          const int w = cy * CW + cx;
+          auto comp = [&](const float4& v) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; };
+#pragma unroll
+          for (int f = 0; f < 3; ++f)
+            W[f * WPL + w] = make_float4(comp(pv[f][0]), comp(pv[f][1]), comp(pv[f][2]), comp(pv[f][3]));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            D[q * WPL + w] = comp(av[q]);
+            if (COMP) D[(4 + q) * WPL + w] = comp(lv[q]);
+          }
         }
       }
-    }
+    } else {
+      for (int t = threadIdx.x; t < CW * CH; t += NT) {
+        const int cx = t % CW, cy = t / CW;
+        const size_t id = (size_t)wrapi(j0 - 2 + cy, ny) * nx + wrapi(i0 - 2 + cx, nx);
 #pragma unroll
-    for (int k = 0; k < PER0; ++k) {
-      const int t = threadIdx.x + k * NT;
-      if (t < NLOAD) {
-#pragma unroll
-        for (int f = 0; f < 3; ++f) W[f * WPL + t] = pv[k][f];
+        for (int f = 0; f < 3; ++f)
+          W[f * WPL + t] = make_float4(__ldg(a.in.pt[f][0] + id), __ldg(a.in.pt[f][1] + id),
+                                       __ldg(a.in.pt[f][2] + id), __ldg(a.in.pt[f][3] + id));
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          D[q * WPL + t] = av[k][q];
-          if (COMP) D[(4 + q) * WPL + t] = lv[k][q];
+          D[q * WPL + t] = __ldg(a.in.avg[q] + id);
+          if (COMP) D[(4 + q) * WPL + t] = __ldg(a.in.lo[q] + id);
         }
       }
     }
@@ -433,7 +447,10 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
   if (bad) atomicOr(a.flags, bad);
 }
 
-constexpr int FUSED_TX = 32, FUSED_TY = 32, FUSED_NT = 512;
+#ifndef AF_FUSED_NT
+#define AF_FUSED_NT 512  // threads per CTA (one CTA per SM: 212 KB of shared memory)
+#endif
+constexpr int FUSED_TX = 32, FUSED_TY = 32, FUSED_NT = AF_FUSED_NT;
 
 template <bool COMP>
 inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a) {
