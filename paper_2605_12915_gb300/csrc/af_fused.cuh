@@ -24,6 +24,21 @@
 #include "af_common.cuh"
 #include "af_ref_kernels.cuh"
 
+// Tile geometry: TX x TY owned cells, NT threads, MINB CTAs per SM (the
+// shared-memory footprint FusedGeom::SMEM must fit MINB times in 228 KB).
+#ifndef AF_FUSED_TX
+#define AF_FUSED_TX 32
+#endif
+#ifndef AF_FUSED_TY
+#define AF_FUSED_TY 32
+#endif
+#ifndef AF_FUSED_NT
+#define AF_FUSED_NT 512
+#endif
+#ifndef AF_FUSED_MINB
+#define AF_FUSED_MINB 1
+#endif
+
 namespace af {
 
 template <int TX_, int TY_>
@@ -116,7 +131,7 @@ __device__ __forceinline__ int foot_axis(int o, float d, float l[3]) {
 }
 
 template <int TX, int TY, int NT, bool COMP>
-__global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
+__global__ void __launch_bounds__(NT, AF_FUSED_MINB) k_fused_step(StepArgs<float> a) {
   using G = FusedGeom<TX, TY>;
   constexpr int CW = G::CW, CH = G::CH, DCW = G::DCW, PW = G::PW;
   constexpr int WPL = G::WPL, DPL = G::DPL, PPL = G::PPL;
@@ -447,10 +462,7 @@ __global__ void __launch_bounds__(NT, 1) k_fused_step(StepArgs<float> a) {
   if (bad) atomicOr(a.flags, bad);
 }
 
-#ifndef AF_FUSED_NT
-#define AF_FUSED_NT 512  // threads per CTA (one CTA per SM: 212 KB of shared memory)
-#endif
-constexpr int FUSED_TX = 32, FUSED_TY = 32, FUSED_NT = AF_FUSED_NT;
+constexpr int FUSED_TX = AF_FUSED_TX, FUSED_TY = AF_FUSED_TY, FUSED_NT = AF_FUSED_NT;
 
 template <bool COMP>
 inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a) {
