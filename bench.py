@@ -37,14 +37,16 @@ N_CELLS_SIDE = 2048
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp32_comp", choices=["fp32", "fp32_comp", "fp64"])
     p.add_argument("--n", type=int, default=N_CELLS_SIDE)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--kernel-reps", type=int, default=20)
+    p.add_argument("--fp64-steps", type=int, default=100,
+                   help="steps of the FP64 comparison run (0: skip)")
     return p.parse_args()
 
 
@@ -55,6 +57,44 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# FP32 arithmetic operations (an FMA counts once) of one cell-update of the
+# fused step, counted from the code: centre recovery ~200, node freezing ~40,
+# acoustic stencils 695 (generated), two Horner evaluations per node ~216,
+# six point updates ~990, space-time Simpson fluxes ~330, compensated update ~144.
+ALU_OPS_PER_CELL = 2600
+FUSED_SOURCES = ["paper_2605_12915_gb300/csrc/af_fused.cuh",
+                 "paper_2605_12915_gb300/csrc/af_common.cuh",
+                 "paper_2605_12915_gb300/csrc/af_stencils.cuh",
+                 "paper_2605_12915_gb300/csrc/af_ref_kernels.cuh"]
+PROFILE = "profiles/k_fused_step_shear2048_fp32comp.md"
+
+
+def fused_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in FUSED_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_cells):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    scaled to n_cells; None if the kernel source changed since the capture."""
+    try:
+        kv = {}
+        with open(os.path.join(ROOT, PROFILE)) as f:
+            for line in f:
+                if ":" in line and not line.startswith(("|", "#", " ")):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != fused_source_hash():
+            return None
+        return float(kv["traffic_bytes_per_launch"]) * n_cells / float(kv["cells_per_launch"])
+    except Exception:
+        return None
 
 
 class ClockSampler:
@@ -109,6 +149,19 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def aggregate(ms_local, n_cells, steps, world, device):
+    """Whole-job throughput of N independent replicas: the slowest rank's time
+    (max over ranks) and the cells all ranks advanced per second."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, n_cells * steps * world / (ms * 1e-3)
 
 
 def dist_setup(args):
@@ -210,12 +263,7 @@ def main():
     barrier()
     ms = ev0.elapsed_time(ev1)
     solver.sync()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * args.steps * world / (ms * 1e-3)
+    ms, value = aggregate(ms, N, args.steps, world, "cuda")
     inv1 = solver.invariants()
 
     # dominant kernel: per-launch duration of the step kernel(s)
@@ -241,9 +289,18 @@ def main():
     hbm, peak_kind = peaks()
     bytes_per_cell = {"fp32": 128, "fp32_comp": 160, "fp64": 256}[args.precision]
     ach = bytes_per_cell * N / (kstats["ms_per_launch"] * 1e-3) / 1e9
+    csum = clocks.summary()
+    sm_hz = 1e6 * (csum["sm_max_mhz"] or 2070.0)
+    alu_peak = 152 * 128 * sm_hz / 1e12
+    alu_ach = ALU_OPS_PER_CELL * N / (kstats["ms_per_launch"] * 1e-3) / 1e12
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": None, "kernel": kstats["kernel"], "peak_kind": peak_kind,
-            "bytes_per_cell": bytes_per_cell}
+            "traffic": profiled_traffic(N) if fused else None, "kernel": kstats["kernel"],
+            "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell,
+            "alu": {"achieved": alu_ach, "peak": alu_peak, "unit": "T FP32 op/s",
+                    "frac": alu_ach / alu_peak, "ops_per_cell": ALU_OPS_PER_CELL,
+                    "note": "the path is issue/ALU bound; peak = 152 SMs x 128 FP32 lanes x SM clock"}}
+    fp64 = fp64_compare(af, I, P, solver_state_after(af, P, args, stream), args, stream, torch) \
+        if args.fp64_steps > 0 else None
     drift = (inv1[:4] - inv0[:4]) / np.array([inv0[0], inv0[0], inv0[0], inv0[3]])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -258,7 +315,8 @@ def main():
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": kstats["launches_per_step"] * args.steps,
-            "clocks": clocks.summary(),
+            "clocks": csum,
+            "fp64": fp64,
             "conservation_drift": [float(x) for x in drift],
             "entropy_change": float(inv1[4] - inv0[4])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -269,6 +327,36 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def solver_state_after(af, P, args, stream):
+    """FP32 state after args.fp64_steps steps from the initial state."""
+    s = af.Solver(P.grid, P.gamma, P.state, precision=args.precision, stream=stream)
+    s.step(P.dt, args.fp64_steps)
+    out = s.state()
+    s.close()
+    return out
+
+
+def fp64_compare(af, I, P, st32, args, stream, torch):
+    """FP64 throughput of the same workload (unfused FP64 kernels) and the
+    FP32-vs-FP64 relative L-inf per plane (max |a-b| / max |b|) after the same
+    number of steps."""
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp64", stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(P.dt, args.fp64_steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.fp64_steps
+    st64 = s.state()
+    s.close()
+    num = np.max(np.abs(st32 - st64), axis=(1, 2))
+    den = np.maximum(np.max(np.abs(st64), axis=(1, 2)), 1e-300)
+    return {"value": P.grid.nx * P.grid.ny / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "steps": args.fp64_steps, "fp32_vs_fp64_rel_linf": float(np.max(num / den)),
+            "fp32_vs_fp64_rel_linf_per_plane": [float(x) for x in num / den]}
 
 
 def solver_kernel_stats(af, solver, P, stream, torch, reps, fused):
