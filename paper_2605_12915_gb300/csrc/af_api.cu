@@ -39,6 +39,7 @@ struct af_handle {
   int red_blocks;
   int broken;
   int fused;             // 1: fused single-pass kernel for the FP32 modes
+  int prefetch_wave;     // resident CTAs of the fused kernel (one wave)
 };
 
 namespace {
@@ -152,6 +153,7 @@ StepArgs<T> step_args(af_handle* h, double dt) {
   a.gas.rho_ref = (T)h->rho_ref;
   a.gas.p_ref = (T)h->p_ref;
   a.variant = (int)h->var;
+  a.prefetch_wave = h->prefetch_wave;
   return a;
 }
 
@@ -290,6 +292,12 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
   // multi-kernel path (same arithmetic, intermediate values in HBM).
   const char* path = getenv("AF_PATH");
   h->fused = (prec != AF_FP64) && !(path && strcmp(path, "ref") == 0);
+  {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const char* pf = getenv("AF_PREFETCH");
+    h->prefetch_wave = (pf && pf[0] == '0') ? 0 : sms * AF_FUSED_MINB;
+  }
   // 2 x 20 state planes + 48 scratch planes, each padded to 256 bytes
   size_t plane = (h->N * h->esize + 255) & ~(size_t)255;
   size_t nplanes = 2 * 20 + 48;

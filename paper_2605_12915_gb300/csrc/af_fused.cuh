@@ -145,6 +145,30 @@ __global__ void __launch_bounds__(NT, AF_FUSED_MINB) k_fused_step(StepArgs<float
   const Gas<float> gas = a.gas;
   unsigned bad = 0;
 
+  // ---- L2 prefetch of the tile that runs one wave later on this GPU ---------
+  // (linear block id + wave size): its phase 0 then reads from L2, not DRAM.
+  {
+    const int wave = a.prefetch_wave;
+    const int nxt = blockIdx.y * gridDim.x + blockIdx.x + wave;
+    if (wave > 0 && nxt < gridDim.x * gridDim.y && (nx & 3) == 0) {
+      const int pi0 = (nxt % gridDim.x) * TX, pj0 = (nxt / gridDim.x) * TY;
+      if (pi0 >= 4 && pj0 >= 2 && pi0 + TX + 4 <= nx && pj0 + CH - 2 <= ny) {
+        constexpr int NPF = 20 * CH;  // one 16-byte-aligned row segment per plane and row
+        for (int t = threadIdx.x; t < NPF; t += NT) {
+          const int plane = t / CH, row = t % CH;
+          if (!COMP && plane >= 16) continue;
+          const float* base = plane < 4 ? a.in.avg[plane]
+                            : plane < 16 ? a.in.pt[(plane - 4) / 4][(plane - 4) % 4]
+                                         : a.in.lo[plane - 16];
+          const float* src = base + (size_t)(pj0 - 2 + row) * nx + (pi0 - 4);
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src),
+                       "r"((unsigned)(sizeof(float) * (TX + 8)))
+                       : "memory");
+        }
+      }
+    }
+  }
+
   // ---- phase 0: every global load of the step, cells [i0-2, i0+TX+4)^2 ------
   // Interior tiles read 16-byte quads of cells [i0-4, i0+TX+4) per row (rows are
   // 16-byte aligned when nx is a multiple of 4); tiles touching the periodic
@@ -275,16 +299,19 @@ __global__ void __launch_bounds__(NT, AF_FUSED_MINB) k_fused_step(StepArgs<float
         LoadW<3, CW, WPL> ld = {W, wc};
         af_sac_C<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
       }
+      // stored: the acoustically evolved velocity u + du, v + dv and the
+      // pressure increment dp (the velocity increments are only ever added to
+      // the interpolated velocity, so they are interpolated together with it)
       float d[3];
       float* D0 = D + fam * 3 * DPL + dc;
       float* D1 = D + (4 + fam) * 3 * DPL + dc;
       increments_at(Gp, Guv, Z, Zinv, 0.5f * r1, d);
-      D0[0] = d[0];
-      D0[DPL] = d[1];
+      D0[0] = wk.y + d[0];
+      D0[DPL] = wk.z + d[1];
       D0[2 * DPL] = d[2];
       increments_at(Gp, Guv, Z, Zinv, r1, d);
-      D1[0] = d[0];
-      D1[DPL] = d[1];
+      D1[0] = wk.y + d[0];
+      D1[DPL] = wk.z + d[1];
       D1[2 * DPL] = d[2];
     }
   }
@@ -327,33 +354,34 @@ __global__ void __launch_bounds__(NT, AF_FUSED_MINB) k_fused_step(StepArgs<float
       iy = foot_axis(oy, clamp1(dfy), ly);
       const int c2 = wcP + iy * CW + ix;
       if (c2 != c1) load_cell<CW, WPL>(W, c2, n);
-      Prim<float> wf;
-      wf.r = AF_Q2(n, x, lx, ly);
-      wf.u = AF_Q2(n, y, lx, ly);
-      wf.v = AF_Q2(n, z, lx, ly);
-      wf.p = AF_Q2(n, w, lx, ly);
-      float d[3];
+      const float rft = AF_Q2(n, x, lx, ly), pft = AF_Q2(n, w, lx, ly);  // rho~_f, p~_f
       Prim<float> nw;
       if (a.variant == 0) {
-        // transported increment at the foot; rho from dp / c_f^2 (Sec. 6.1 step 4)
+        // transported increment at the foot; rho from dp / c_f^2 (Sec. 6.1 step 4):
+        // u_f + du_f = I_h(u + du)(P_f) since both interpolants share the basis
         const int dcf = (py + 1 + iy) * DCW + (px + 1 + ix);  // D cell of the foot cell
+        float e[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-          d[q] = q2_eval<DCW>(Ds + (0 * 3 + q) * DPL, Ds + (1 * 3 + q) * DPL,
+          e[q] = q2_eval<DCW>(Ds + (0 * 3 + q) * DPL, Ds + (1 * 3 + q) * DPL,
                               Ds + (2 * 3 + q) * DPL, Ds + (3 * 3 + q) * DPL, dcf, lx, ly);
-        const float rf = gas.rho_ref + wf.r, pf = gas.p_ref + wf.p;
+        const float rf = gas.rho_ref + rft, pf = gas.p_ref + pft;
         if (!(rf > 0.f && pf > 0.f)) bad |= FLAG_NONPHYSICAL;
-        nw.r = wf.r + d[2] * rf / (gas.gamma * pf);
+        nw.r = rft + e[2] * rf / (gas.gamma * pf);
+        nw.u = e[0];
+        nw.v = e[1];
+        nw.p = pft + e[2];
       } else {
         // additive update (Eq. barsukow-additive), acoustic rho closure at P
         const int dcp = (py + 1) * DCW + (px + 1);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) d[q] = Ds[(fam * 3 + q) * DPL + dcp];
-        nw.r = wf.r + d[2] * (gas.rho_ref + wp.x) / (gas.gamma * (gas.p_ref + wp.w));
+        const float du = Ds[(fam * 3 + 0) * DPL + dcp] - wp.y;
+        const float dv = Ds[(fam * 3 + 1) * DPL + dcp] - wp.z;
+        const float dp = Ds[(fam * 3 + 2) * DPL + dcp];
+        nw.r = rft + dp * (gas.rho_ref + wp.x) / (gas.gamma * (gas.p_ref + wp.w));
+        nw.u = AF_Q2(n, y, lx, ly) + du;
+        nw.v = AF_Q2(n, z, lx, ly) + dv;
+        nw.p = pft + dp;
       }
-      nw.u = wf.u + d[0];
-      nw.v = wf.v + d[1];
-      nw.p = wf.p + d[2];
       if (!(isfinite(nw.r) && isfinite(nw.u) && isfinite(nw.v) && isfinite(nw.p)))
         bad |= FLAG_NONFINITE;
       res[k] = make_float4(nw.r, nw.u, nw.v, nw.p);

@@ -123,6 +123,7 @@ extern "C" af_status af_step_noalloc(const af_grid* g, double gamma, double dt, 
   a.gas.rho_ref = 0.0;
   a.gas.p_ref = 0.0;
   a.variant = (int)var;
+  a.prefetch_wave = 0;
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // the work area keeps the previous call's contents: the error word must start at 0

@@ -28,6 +28,7 @@ struct StepArgs {
   T h, dt;
   Gas<T> gas;
   int variant;        // 0 TAI, 1 RB
+  int prefetch_wave;  // fused kernel: blocks per wave for the L2 prefetch (0: none)
 };
 
 template <typename T>
