@@ -123,6 +123,18 @@ af_status af_set_state(af_handle *h, const af_state_f64 *in, af_memory where);
  * Synchronises the stream. */
 af_status af_reduce_invariants(af_handle *h, double *out);
 
+/* Discrete adjoint of one step (Sec. 6.1, differentiated by hand, stage by
+ * stage): lam_out = (d state^{n+1} / d state^n)^T lam_in, linearised about the
+ * handle's current state (state^n), which is left unchanged.  lam_in holds the
+ * adjoint of the state after one step of size dt, lam_out receives the adjoint
+ * of the current state; both are FP64 arrays in the state layout above, on
+ * `where`, owned by the caller (they may not overlap).  Adjoints are with
+ * respect to the stored variables (cell averages and primitive point values).
+ * The step's forward intermediates are recomputed in the handle's precision.
+ * Synchronises the stream; returns the latched device error, if any. */
+af_status af_adjoint_step(af_handle *h, double dt, const af_state_f64 *lam_in,
+                          const af_state_f64 *lam_out, af_memory where);
+
 /* Release the handle's device memory and streams' resources.  NULL is a no-op. */
 void af_destroy(af_handle *h);
 

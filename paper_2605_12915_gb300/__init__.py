@@ -71,6 +71,9 @@ def load():
         lib.af_set_state.restype = ctypes.c_int
         lib.af_reduce_invariants.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.af_reduce_invariants.restype = ctypes.c_int
+        lib.af_adjoint_step.argtypes = [vp, d, ctypes.POINTER(AfState), ctypes.POINTER(AfState),
+                                        ctypes.c_int]
+        lib.af_adjoint_step.restype = ctypes.c_int
         lib.af_destroy.argtypes = [vp]
         lib.af_destroy.restype = None
         lib.af_status_string.argtypes = [ctypes.c_int]
@@ -159,6 +162,18 @@ def af_reduce_invariants(handle, out):
                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
 
+def af_adjoint_step(handle, dt, lam_in, lam_out):
+    """lam_out = (d state^{n+1}/d state^n)^T lam_in about the handle's current state.
+    Both (16, ny, nx) float64, both on the host (numpy) or both on the device (torch)."""
+    pin, din = _array_ptr(lam_in)
+    pout, dout = _array_ptr(lam_out)
+    assert din == dout, "lam_in and lam_out must both be host or both be device arrays"
+    n = lam_in.shape[1] * lam_in.shape[2]
+    si, so = _state_struct(pin, n), _state_struct(pout, n)
+    return load().af_adjoint_step(ctypes.c_void_p(handle), float(dt), ctypes.byref(si),
+                                  ctypes.byref(so), AF_DEVICE if din else AF_HOST)
+
+
 def af_destroy(handle):
     if handle:
         load().af_destroy(ctypes.c_void_p(handle))
@@ -209,6 +224,19 @@ class Solver:
         if rc != AF_OK:
             raise AfError(rc, "af_reduce_invariants")
         return out
+
+    def adjoint(self, dt, lam_in, lam_out=None):
+        """Adjoint of one step about the current state (see af_adjoint_step)."""
+        if lam_out is None:
+            if hasattr(lam_in, "data_ptr"):
+                lam_out = lam_in.new_empty(lam_in.shape)
+            else:
+                import numpy as np
+                lam_out = np.empty_like(lam_in)
+        rc = af_adjoint_step(self.handle, dt, lam_in, lam_out)
+        if rc != AF_OK:
+            raise AfError(rc, "af_adjoint_step")
+        return lam_out
 
     def close(self):
         if self.handle:

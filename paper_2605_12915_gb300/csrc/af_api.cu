@@ -14,6 +14,7 @@
 #include "af_reduce.cuh"
 #include "af_ref_kernels.cuh"
 #include "af_fused.cuh"
+#include "af_adjoint.cuh"
 
 using namespace af;
 
@@ -40,6 +41,7 @@ struct af_handle {
   int broken;
   int fused;             // 1: fused single-pass kernel for the FP32 modes
   int prefetch_wave;     // resident CTAs of the fused kernel (one wave)
+  void* adj_arena;       // adjoint planes (lazy): lin 16, lout 16, lwc 4, linc 24, lhalf 12, lfull 12
 };
 
 namespace {
@@ -114,6 +116,13 @@ __global__ void k_export(Planes<T> src, F64Out dst, size_t N, Offsets o) {
         dst.p[4 + 4 * f + k][id] =
             (double)src.pt[f][k][id] + (k == 0 ? o.rho : (k == 3 ? o.p : 0.0));
   }
+}
+
+template <typename A, typename B>
+__global__ void k_cast(const A* src, B* dst, size_t N) {
+  for (size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x; id < N;
+       id += (size_t)gridDim.x * blockDim.x)
+    dst[id] = (B)src[id];
 }
 
 Offsets offsets_of(const af_handle* h) {
@@ -241,6 +250,85 @@ af_status import_state(af_handle* h, const af_state_f64* in, af_memory where) {
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
   *(volatile unsigned*)h->h_flags = 0;
   return AF_OK;
+}
+
+}  // namespace
+extern "C" af_status af_sync(af_handle* h);
+namespace {
+
+template <typename T, bool COMP>
+af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const af_state_f64* lout,
+                       af_memory where) {
+  const size_t plane = (h->N * sizeof(T) + 255) & ~(size_t)255;
+  const int NPL = 84;
+  if (!h->adj_arena && cudaMalloc(&h->adj_arena, plane * NPL) != cudaSuccess) {
+    h->adj_arena = nullptr;
+    return AF_ERR_ALLOC;
+  }
+  char* base = (char*)h->adj_arena;
+  auto P = [&](int k) { return (T*)(base + plane * (size_t)k); };
+  AdjArgs<T> a;
+  a.f = step_args<T>(h, dt);
+  int k = 0;
+  for (int q = 0; q < 16; ++q) a.lin[q] = P(k++);
+  for (int q = 0; q < 16; ++q) a.lout[q] = P(k++);
+  for (int q = 0; q < 4; ++q) a.lwc[q] = P(k++);
+  const int linc0 = k;
+  for (int s2 = 0; s2 < 2; ++s2)
+    for (int f = 0; f < 4; ++f)
+      for (int q = 0; q < 3; ++q) a.linc[s2][f][q] = P(k++);
+  for (int f = 0; f < 3; ++f)
+    for (int q = 0; q < 4; ++q) a.lhalf[f][q] = P(k++);
+  for (int f = 0; f < 3; ++f)
+    for (int q = 0; q < 4; ++q) a.lfull[f][q] = P(k++);
+  cudaStream_t s = h->stream;
+  // lambda^{n+1} in (FP64 -> working precision, no storage offsets)
+  af_status st = ensure_staging(h);
+  if (st != AF_OK) return st;
+  for (int p = 0; p < 16; ++p) {
+    const double* src = plane_in(lin, p);
+    if (where == AF_HOST) {
+      if (cudaMemcpyAsync(h->staging + (size_t)p * h->N, src, sizeof(double) * h->N,
+                          cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return cuda_fail(h);
+      src = h->staging + (size_t)p * h->N;
+    }
+    k_cast<<<grid1d(h->N), 256, 0, s>>>(src, a.lin[p], h->N);
+  }
+  // forward intermediates of the step from the handle's current state
+  dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
+  k_center<T, COMP><<<grd, blk, 0, s>>>(a.f);
+  k_acoustic<0, T><<<grd, blk, 0, s>>>(a.f);
+  k_acoustic<1, T><<<grd, blk, 0, s>>>(a.f);
+  k_acoustic<2, T><<<grd, blk, 0, s>>>(a.f);
+  k_acoustic<3, T><<<grd, blk, 0, s>>>(a.f);
+  k_points<0, T><<<grd, blk, 0, s>>>(a.f);
+  k_points<1, T><<<grd, blk, 0, s>>>(a.f);
+  k_points<2, T><<<grd, blk, 0, s>>>(a.f);
+  // reverse sweep
+  if (cudaMemsetAsync(a.lwc[0], 0, plane * 4, s) != cudaSuccess ||
+      cudaMemsetAsync(P(linc0), 0, plane * 24, s) != cudaSuccess)
+    return cuda_fail(h);
+  k_adj_flux<T><<<grd, blk, 0, s>>>(a);
+  k_adj_points<0, T><<<grd, blk, 0, s>>>(a);
+  k_adj_points<1, T><<<grd, blk, 0, s>>>(a);
+  k_adj_points<2, T><<<grd, blk, 0, s>>>(a);
+  k_adj_acoustic<0, T><<<grd, blk, 0, s>>>(a);
+  k_adj_acoustic<1, T><<<grd, blk, 0, s>>>(a);
+  k_adj_acoustic<2, T><<<grd, blk, 0, s>>>(a);
+  k_adj_acoustic<3, T><<<grd, blk, 0, s>>>(a);
+  k_adj_center<T, COMP><<<grd, blk, 0, s>>>(a);
+  // lambda^n out
+  for (int p = 0; p < 16; ++p) {
+    double* dst = where == AF_HOST ? h->staging + (size_t)p * h->N : (double*)plane_in(lout, p);
+    k_cast<<<grid1d(h->N), 256, 0, s>>>(a.lout[p], dst, h->N);
+    if (where == AF_HOST &&
+        cudaMemcpyAsync((void*)plane_in(lout, p), dst, sizeof(double) * h->N,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return cuda_fail(h);
+  }
+  if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+  return af_sync(h);
 }
 
 }  // namespace
@@ -458,6 +546,21 @@ af_status af_reduce_invariants(af_handle* h, double* out) {
   return st;
 }
 
+af_status af_adjoint_step(af_handle* h, double dt, const af_state_f64* lam_in,
+                          const af_state_f64* lam_out, af_memory where) {
+  if (!h || !(dt > 0.0) || check_state_ptrs(lam_in) != AF_OK ||
+      check_state_ptrs(lam_out) != AF_OK || (where != AF_HOST && where != AF_DEVICE))
+    return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  DeviceGuard guard(h->device);
+  switch (h->prec) {
+    case AF_FP64: return adjoint_impl<double, false>(h, dt, lam_in, lam_out, where);
+    case AF_FP32: return adjoint_impl<float, false>(h, dt, lam_in, lam_out, where);
+    case AF_FP32_COMP: return adjoint_impl<float, true>(h, dt, lam_in, lam_out, where);
+  }
+  return AF_ERR_ARG;
+}
+
 void af_destroy(af_handle* h) {
   if (!h) return;
   DeviceGuard guard(h->device);
@@ -467,6 +570,7 @@ void af_destroy(af_handle* h) {
   if (h->d_flags) cudaFree(h->d_flags);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->d_red) cudaFree(h->d_red);
+  if (h->adj_arena) cudaFree(h->adj_arena);
   if (h->h_red) cudaFreeHost(h->h_red);
   delete h;
 }

@@ -325,6 +325,131 @@ __device__ __forceinline__ void af_sac_V(const Load& L, T pK, T uK, T vK, T Gp[3
   }
 }
 
+// family V, transposed: lattice adjoints from output adjoints
+template <typename T, typename Scatter>
+__device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4], const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
+  {  // orbit (+-0, +-1) half cells
+    const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(5.0), lGp[0][2], fma(T(-5.81971863420548805845), lGp[0][1], fma(T(2.0), lGp[0][0], T(0)))));
+    const T leop = fma(T(1.0), lGp[2][3], fma(T(-3.87981242280365870564), lGp[2][2], fma(T(5.0), lGp[2][1], fma(T(-2.0), lGp[2][0], T(0)))));
+    const T leeu = fma(T(-0.666666666666666666667), lGuv[1][3], fma(T(2.33333333333333333333), lGuv[1][2], fma(T(-1.90985931710274402923), lGuv[1][1], T(0))));
+    const T leev = fma(T(-0.666666666666666666667), lGuv[2][3], fma(T(2.66666666666666666667), lGuv[2][2], fma(T(-3.90985931710274402923), lGuv[2][1], fma(T(2.0), lGuv[2][0], T(0)))));
+    const T leov = fma(T(1.0), lGuv[0][3], fma(T(-3.87981242280365870564), lGuv[0][2], fma(T(5.0), lGuv[0][1], fma(T(-2.0), lGuv[0][0], T(0)))));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(0, 1, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
+    S(0, -1, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+  }
+  {  // orbit (+-0, +-2) half cells
+    const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-2.0), lGp[0][2], fma(T(1.95492965855137201461), lGp[0][1], fma(T(-0.5), lGp[0][0], T(0)))));
+    const T leop = fma(T(-0.5), lGp[2][3], fma(T(1.60657287806849601948), lGp[2][2], fma(T(-1.75), lGp[2][1], fma(T(0.5), lGp[2][0], T(0)))));
+    const T leeu = fma(T(0.333333333333333333333), lGuv[1][3], fma(T(-0.833333333333333333333), lGuv[1][2], fma(T(0.477464829275686007307), lGuv[1][1], T(0))));
+    const T leev = fma(T(0.333333333333333333333), lGuv[2][3], fma(T(-1.16666666666666666667), lGuv[2][2], fma(T(1.47746482927568600731), lGuv[2][1], fma(T(-0.5), lGuv[2][0], T(0)))));
+    const T leov = fma(T(-0.5), lGuv[0][3], fma(T(1.60657287806849601948), lGuv[0][2], fma(T(-1.75), lGuv[0][1], fma(T(0.5), lGuv[0][0], T(0)))));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(0, 2, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
+    S(0, -2, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+  }
+  {  // orbit (+-1, +-0) half cells
+    const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(5.0), lGp[0][2], fma(T(-5.81971863420548805845), lGp[0][1], fma(T(2.0), lGp[0][0], T(0)))));
+    const T loep = fma(T(1.0), lGp[1][3], fma(T(-3.87981242280365870564), lGp[1][2], fma(T(5.0), lGp[1][1], fma(T(-2.0), lGp[1][0], T(0)))));
+    const T leeu = fma(T(-0.666666666666666666667), lGuv[1][3], fma(T(2.66666666666666666667), lGuv[1][2], fma(T(-3.90985931710274402923), lGuv[1][1], fma(T(2.0), lGuv[1][0], T(0)))));
+    const T loeu = fma(T(1.0), lGuv[0][3], fma(T(-3.87981242280365870564), lGuv[0][2], fma(T(5.0), lGuv[0][1], fma(T(-2.0), lGuv[0][0], T(0)))));
+    const T leev = fma(T(-0.666666666666666666667), lGuv[2][3], fma(T(2.33333333333333333333), lGuv[2][2], fma(T(-1.90985931710274402923), lGuv[2][1], T(0))));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
+    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+  }
+  {  // orbit (+-1, +-1) half cells
+    const T leep = fma(T(1.33333333333333333333), lGp[0][3], fma(T(-4.0), lGp[0][2], fma(T(2.5464790894703253723), lGp[0][1], T(0))));
+    const T loep = fma(T(-1.0), lGp[1][3], fma(T(3.03098605964688358153), lGp[1][2], fma(T(-2.0), lGp[1][1], T(0))));
+    const T leop = fma(T(-1.0), lGp[2][3], fma(T(3.03098605964688358153), lGp[2][2], fma(T(-2.0), lGp[2][1], T(0))));
+    const T leeu = fma(T(0.666666666666666666667), lGuv[1][3], fma(T(-2.0), lGuv[1][2], fma(T(1.27323954473516268615), lGuv[1][1], T(0))));
+    const T loeu = fma(T(-1.0), lGuv[0][3], fma(T(3.03098605964688358153), lGuv[0][2], fma(T(-2.0), lGuv[0][1], T(0))));
+    const T loou = fma(T(0.848826363156775124101), lGuv[2][3], fma(T(-2.66666666666666666667), lGuv[2][2], fma(T(2.0), lGuv[2][1], T(0))));
+    const T leev = fma(T(0.666666666666666666667), lGuv[2][3], fma(T(-2.0), lGuv[2][2], fma(T(1.27323954473516268615), lGuv[2][1], T(0))));
+    const T leov = fma(T(-1.0), lGuv[0][3], fma(T(3.03098605964688358153), lGuv[0][2], fma(T(-2.0), lGuv[0][1], T(0))));
+    const T loov = fma(T(0.848826363156775124101), lGuv[1][3], fma(T(-2.66666666666666666667), lGuv[1][2], fma(T(2.0), lGuv[1][1], T(0))));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+  }
+  {  // orbit (+-1, +-2) half cells
+    const T leep = fma(T(-0.666666666666666666667), lGp[0][3], fma(T(1.5), lGp[0][2], fma(T(-0.636619772367581343076), lGp[0][1], T(0))));
+    const T loep = fma(T(0.5), lGp[1][3], fma(T(-1.09107984824505422872), lGp[1][2], fma(T(0.5), lGp[1][1], T(0))));
+    const T leop = fma(T(0.5), lGp[2][3], fma(T(-1.18215969649010845743), lGp[2][2], fma(T(0.5), lGp[2][1], T(0))));
+    const T leeu = fma(T(-0.333333333333333333333), lGuv[1][3], fma(T(0.666666666666666666667), lGuv[1][2], fma(T(-0.318309886183790671538), lGuv[1][1], T(0))));
+    const T loeu = fma(T(0.5), lGuv[0][3], fma(T(-1.09107984824505422872), lGuv[0][2], fma(T(0.5), lGuv[0][1], T(0))));
+    const T loou = fma(T(-0.42441318157838756205), lGuv[2][3], fma(T(1.0), lGuv[2][2], fma(T(-0.5), lGuv[2][1], T(0))));
+    const T leev = fma(T(-0.333333333333333333333), lGuv[2][3], fma(T(0.833333333333333333333), lGuv[2][2], fma(T(-0.318309886183790671538), lGuv[2][1], T(0))));
+    const T leov = fma(T(0.5), lGuv[0][3], fma(T(-1.18215969649010845743), lGuv[0][2], fma(T(0.5), lGuv[0][1], T(0))));
+    const T loov = fma(T(-0.42441318157838756205), lGuv[1][3], fma(T(1.0), lGuv[1][2], fma(T(-0.5), lGuv[1][1], T(0))));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(1, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(1, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-1, 2, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-1, -2, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+  }
+  {  // orbit (+-2, +-0) half cells
+    const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-2.0), lGp[0][2], fma(T(1.95492965855137201461), lGp[0][1], fma(T(-0.5), lGp[0][0], T(0)))));
+    const T loep = fma(T(-0.5), lGp[1][3], fma(T(1.60657287806849601948), lGp[1][2], fma(T(-1.75), lGp[1][1], fma(T(0.5), lGp[1][0], T(0)))));
+    const T leeu = fma(T(0.333333333333333333333), lGuv[1][3], fma(T(-1.16666666666666666667), lGuv[1][2], fma(T(1.47746482927568600731), lGuv[1][1], fma(T(-0.5), lGuv[1][0], T(0)))));
+    const T loeu = fma(T(-0.5), lGuv[0][3], fma(T(1.60657287806849601948), lGuv[0][2], fma(T(-1.75), lGuv[0][1], fma(T(0.5), lGuv[0][0], T(0)))));
+    const T leev = fma(T(0.333333333333333333333), lGuv[2][3], fma(T(-0.833333333333333333333), lGuv[2][2], fma(T(0.477464829275686007307), lGuv[2][1], T(0))));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(2, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
+    S(-2, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+  }
+  {  // orbit (+-2, +-1) half cells
+    const T leep = fma(T(-0.666666666666666666667), lGp[0][3], fma(T(1.5), lGp[0][2], fma(T(-0.636619772367581343076), lGp[0][1], T(0))));
+    const T loep = fma(T(0.5), lGp[1][3], fma(T(-1.18215969649010845743), lGp[1][2], fma(T(0.5), lGp[1][1], T(0))));
+    const T leop = fma(T(0.5), lGp[2][3], fma(T(-1.09107984824505422872), lGp[2][2], fma(T(0.5), lGp[2][1], T(0))));
+    const T leeu = fma(T(-0.333333333333333333333), lGuv[1][3], fma(T(0.833333333333333333333), lGuv[1][2], fma(T(-0.318309886183790671538), lGuv[1][1], T(0))));
+    const T loeu = fma(T(0.5), lGuv[0][3], fma(T(-1.18215969649010845743), lGuv[0][2], fma(T(0.5), lGuv[0][1], T(0))));
+    const T loou = fma(T(-0.42441318157838756205), lGuv[2][3], fma(T(1.0), lGuv[2][2], fma(T(-0.5), lGuv[2][1], T(0))));
+    const T leev = fma(T(-0.333333333333333333333), lGuv[2][3], fma(T(0.666666666666666666667), lGuv[2][2], fma(T(-0.318309886183790671538), lGuv[2][1], T(0))));
+    const T leov = fma(T(0.5), lGuv[0][3], fma(T(-1.09107984824505422872), lGuv[0][2], fma(T(0.5), lGuv[0][1], T(0))));
+    const T loov = fma(T(-0.42441318157838756205), lGuv[1][3], fma(T(1.0), lGuv[1][2], fma(T(-0.5), lGuv[1][1], T(0))));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-2, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-2, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+  }
+  {  // orbit (+-2, +-2) half cells
+    const T leep = fma(T(0.333333333333333333333), lGp[0][3], fma(T(-0.5), lGp[0][2], fma(T(0.159154943091895335769), lGp[0][1], T(0))));
+    const T loep = fma(T(-0.25), lGp[1][3], fma(T(0.378873257455860447692), lGp[1][2], fma(T(-0.125), lGp[1][1], T(0))));
+    const T leop = fma(T(-0.25), lGp[2][3], fma(T(0.378873257455860447692), lGp[2][2], fma(T(-0.125), lGp[2][1], T(0))));
+    const T leeu = fma(T(0.166666666666666666667), lGuv[1][3], fma(T(-0.25), lGuv[1][2], fma(T(0.0795774715459476678844), lGuv[1][1], T(0))));
+    const T loeu = fma(T(-0.25), lGuv[0][3], fma(T(0.378873257455860447692), lGuv[0][2], fma(T(-0.125), lGuv[0][1], T(0))));
+    const T loou = fma(T(0.212206590789193781025), lGuv[2][3], fma(T(-0.333333333333333333333), lGuv[2][2], fma(T(0.125), lGuv[2][1], T(0))));
+    const T leev = fma(T(0.166666666666666666667), lGuv[2][3], fma(T(-0.25), lGuv[2][2], fma(T(0.0795774715459476678844), lGuv[2][1], T(0))));
+    const T leov = fma(T(-0.25), lGuv[0][3], fma(T(0.378873257455860447692), lGuv[0][2], fma(T(-0.125), lGuv[0][1], T(0))));
+    const T loov = fma(T(0.212206590789193781025), lGuv[1][3], fma(T(-0.333333333333333333333), lGuv[1][2], fma(T(0.125), lGuv[1][1], T(0))));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(2, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(2, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-2, 2, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-2, -2, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+  }
+}
+
 // family EV: 5 orbit representatives
 template <typename T, typename Load>
 __device__ __forceinline__ void af_sac_EV(const Load& L, T pK, T uK, T vK, T Gp[3][4], T Guv[3][4]) {
@@ -486,6 +611,83 @@ __device__ __forceinline__ void af_sac_EV(const Load& L, T pK, T uK, T vK, T Gp[
     Guv[2][2] = fma(T(0.333333333333333333333), oou, Guv[2][2]);
     Guv[2][2] = fma(T(-0.333333333333333333333), eev, Guv[2][2]);
     Guv[2][3] = fma(T(0.333333333333333333333), eev, Guv[2][3]);
+  }
+}
+
+// family EV, transposed: lattice adjoints from output adjoints
+template <typename T, typename Scatter>
+__device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4], const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
+  {  // orbit (+-0, +-1) half cells
+    const T leep = fma(T(1.33333333333333333333), lGp[0][3], fma(T(-3.0), lGp[0][2], fma(T(2.0), lGp[0][1], T(0))));
+    const T leop = fma(T(-0.666666666666666666667), lGp[2][2], fma(T(1.5), lGp[2][1], fma(T(-1.0), lGp[2][0], T(0))));
+    const T leeu = fma(T(0.666666666666666666667), lGuv[1][3], fma(T(-1.0), lGuv[1][2], T(0)));
+    const T leev = fma(T(0.666666666666666666667), lGuv[2][3], fma(T(-2.0), lGuv[2][2], fma(T(2.0), lGuv[2][1], T(0))));
+    const T leov = fma(T(-0.666666666666666666667), lGuv[0][2], fma(T(1.5), lGuv[0][1], fma(T(-1.0), lGuv[0][0], T(0))));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(0, 1, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
+    S(0, -1, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+  }
+  {  // orbit (+-1, +-0) half cells
+    const T leep = fma(T(2.66666666666666666667), lGp[0][3], fma(T(-4.0), lGp[0][2], fma(T(-2.0), lGp[0][1], fma(T(2.0), lGp[0][0], T(0)))));
+    const T loep = fma(T(-2.0), lGp[1][3], fma(T(2.66666666666666666667), lGp[1][2], fma(T(2.0), lGp[1][1], fma(T(-2.0), lGp[1][0], T(0)))));
+    const T leeu = fma(T(1.33333333333333333333), lGuv[1][3], fma(T(-1.33333333333333333333), lGuv[1][2], fma(T(-2.0), lGuv[1][1], fma(T(2.0), lGuv[1][0], T(0)))));
+    const T loeu = fma(T(-2.0), lGuv[0][3], fma(T(2.66666666666666666667), lGuv[0][2], fma(T(2.0), lGuv[0][1], fma(T(-2.0), lGuv[0][0], T(0)))));
+    const T leev = fma(T(1.33333333333333333333), lGuv[2][3], fma(T(-2.66666666666666666667), lGuv[2][2], T(0)));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
+    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+  }
+  {  // orbit (+-1, +-1) half cells
+    const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(2.0), lGp[0][2], T(0)));
+    const T loep = fma(T(1.0), lGp[1][3], fma(T(-1.33333333333333333333), lGp[1][2], T(0)));
+    const T leop = fma(T(0.666666666666666666667), lGp[2][2], fma(T(-1.0), lGp[2][1], T(0)));
+    const T leeu = fma(T(-0.666666666666666666667), lGuv[1][3], fma(T(0.666666666666666666667), lGuv[1][2], T(0)));
+    const T loeu = fma(T(1.0), lGuv[0][3], fma(T(-1.33333333333333333333), lGuv[0][2], T(0)));
+    const T loou = fma(T(-0.666666666666666666667), lGuv[2][2], fma(T(1.0), lGuv[2][1], T(0)));
+    const T leev = fma(T(-0.666666666666666666667), lGuv[2][3], fma(T(1.33333333333333333333), lGuv[2][2], T(0)));
+    const T leov = fma(T(0.666666666666666666667), lGuv[0][2], fma(T(-1.0), lGuv[0][1], T(0)));
+    const T loov = fma(T(-0.666666666666666666667), lGuv[1][2], fma(T(1.0), lGuv[1][1], T(0)));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+  }
+  {  // orbit (+-2, +-0) half cells
+    const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(1.0), lGp[0][2], fma(T(1.0), lGp[0][1], fma(T(-0.5), lGp[0][0], T(0)))));
+    const T loep = fma(T(1.0), lGp[1][3], fma(T(-0.666666666666666666667), lGp[1][2], fma(T(-1.0), lGp[1][1], fma(T(0.5), lGp[1][0], T(0)))));
+    const T leeu = fma(T(-0.666666666666666666667), lGuv[1][3], fma(T(0.333333333333333333333), lGuv[1][2], fma(T(1.0), lGuv[1][1], fma(T(-0.5), lGuv[1][0], T(0)))));
+    const T loeu = fma(T(1.0), lGuv[0][3], fma(T(-0.666666666666666666667), lGuv[0][2], fma(T(-1.0), lGuv[0][1], fma(T(0.5), lGuv[0][0], T(0)))));
+    const T leev = fma(T(-0.666666666666666666667), lGuv[2][3], fma(T(0.666666666666666666667), lGuv[2][2], T(0)));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(2, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
+    S(-2, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+  }
+  {  // orbit (+-2, +-1) half cells
+    const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-0.5), lGp[0][2], T(0)));
+    const T loep = fma(T(-0.5), lGp[1][3], fma(T(0.333333333333333333333), lGp[1][2], T(0)));
+    const T leop = fma(T(-0.333333333333333333333), lGp[2][2], fma(T(0.25), lGp[2][1], T(0)));
+    const T leeu = fma(T(0.333333333333333333333), lGuv[1][3], fma(T(-0.166666666666666666667), lGuv[1][2], T(0)));
+    const T loeu = fma(T(-0.5), lGuv[0][3], fma(T(0.333333333333333333333), lGuv[0][2], T(0)));
+    const T loou = fma(T(0.333333333333333333333), lGuv[2][2], fma(T(-0.25), lGuv[2][1], T(0)));
+    const T leev = fma(T(0.333333333333333333333), lGuv[2][3], fma(T(-0.333333333333333333333), lGuv[2][2], T(0)));
+    const T leov = fma(T(-0.333333333333333333333), lGuv[0][2], fma(T(0.25), lGuv[0][1], T(0)));
+    const T loov = fma(T(0.333333333333333333333), lGuv[1][2], fma(T(-0.25), lGuv[1][1], T(0)));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-2, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-2, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
 }
 
@@ -653,6 +855,83 @@ __device__ __forceinline__ void af_sac_EH(const Load& L, T pK, T uK, T vK, T Gp[
   }
 }
 
+// family EH, transposed: lattice adjoints from output adjoints
+template <typename T, typename Scatter>
+__device__ __forceinline__ void af_sac_EH_adj(const Scatter& S, const T lGp[3][4], const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
+  {  // orbit (+-0, +-1) half cells
+    const T leep = fma(T(2.66666666666666666667), lGp[0][3], fma(T(-4.0), lGp[0][2], fma(T(-2.0), lGp[0][1], fma(T(2.0), lGp[0][0], T(0)))));
+    const T leop = fma(T(-2.0), lGp[2][3], fma(T(2.66666666666666666667), lGp[2][2], fma(T(2.0), lGp[2][1], fma(T(-2.0), lGp[2][0], T(0)))));
+    const T leeu = fma(T(1.33333333333333333333), lGuv[1][3], fma(T(-2.66666666666666666667), lGuv[1][2], T(0)));
+    const T leev = fma(T(1.33333333333333333333), lGuv[2][3], fma(T(-1.33333333333333333333), lGuv[2][2], fma(T(-2.0), lGuv[2][1], fma(T(2.0), lGuv[2][0], T(0)))));
+    const T leov = fma(T(-2.0), lGuv[0][3], fma(T(2.66666666666666666667), lGuv[0][2], fma(T(2.0), lGuv[0][1], fma(T(-2.0), lGuv[0][0], T(0)))));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(0, 1, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
+    S(0, -1, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+  }
+  {  // orbit (+-0, +-2) half cells
+    const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(1.0), lGp[0][2], fma(T(1.0), lGp[0][1], fma(T(-0.5), lGp[0][0], T(0)))));
+    const T leop = fma(T(1.0), lGp[2][3], fma(T(-0.666666666666666666667), lGp[2][2], fma(T(-1.0), lGp[2][1], fma(T(0.5), lGp[2][0], T(0)))));
+    const T leeu = fma(T(-0.666666666666666666667), lGuv[1][3], fma(T(0.666666666666666666667), lGuv[1][2], T(0)));
+    const T leev = fma(T(-0.666666666666666666667), lGuv[2][3], fma(T(0.333333333333333333333), lGuv[2][2], fma(T(1.0), lGuv[2][1], fma(T(-0.5), lGuv[2][0], T(0)))));
+    const T leov = fma(T(1.0), lGuv[0][3], fma(T(-0.666666666666666666667), lGuv[0][2], fma(T(-1.0), lGuv[0][1], fma(T(0.5), lGuv[0][0], T(0)))));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(0, 2, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
+    S(0, -2, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+  }
+  {  // orbit (+-1, +-0) half cells
+    const T leep = fma(T(1.33333333333333333333), lGp[0][3], fma(T(-3.0), lGp[0][2], fma(T(2.0), lGp[0][1], T(0))));
+    const T loep = fma(T(-0.666666666666666666667), lGp[1][2], fma(T(1.5), lGp[1][1], fma(T(-1.0), lGp[1][0], T(0))));
+    const T leeu = fma(T(0.666666666666666666667), lGuv[1][3], fma(T(-2.0), lGuv[1][2], fma(T(2.0), lGuv[1][1], T(0))));
+    const T loeu = fma(T(-0.666666666666666666667), lGuv[0][2], fma(T(1.5), lGuv[0][1], fma(T(-1.0), lGuv[0][0], T(0))));
+    const T leev = fma(T(0.666666666666666666667), lGuv[2][3], fma(T(-1.0), lGuv[2][2], T(0)));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
+    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+  }
+  {  // orbit (+-1, +-1) half cells
+    const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(2.0), lGp[0][2], T(0)));
+    const T loep = fma(T(0.666666666666666666667), lGp[1][2], fma(T(-1.0), lGp[1][1], T(0)));
+    const T leop = fma(T(1.0), lGp[2][3], fma(T(-1.33333333333333333333), lGp[2][2], T(0)));
+    const T leeu = fma(T(-0.666666666666666666667), lGuv[1][3], fma(T(1.33333333333333333333), lGuv[1][2], T(0)));
+    const T loeu = fma(T(0.666666666666666666667), lGuv[0][2], fma(T(-1.0), lGuv[0][1], T(0)));
+    const T loou = fma(T(-0.666666666666666666667), lGuv[2][2], fma(T(1.0), lGuv[2][1], T(0)));
+    const T leev = fma(T(-0.666666666666666666667), lGuv[2][3], fma(T(0.666666666666666666667), lGuv[2][2], T(0)));
+    const T leov = fma(T(1.0), lGuv[0][3], fma(T(-1.33333333333333333333), lGuv[0][2], T(0)));
+    const T loov = fma(T(-0.666666666666666666667), lGuv[1][2], fma(T(1.0), lGuv[1][1], T(0)));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+  }
+  {  // orbit (+-1, +-2) half cells
+    const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-0.5), lGp[0][2], T(0)));
+    const T loep = fma(T(-0.333333333333333333333), lGp[1][2], fma(T(0.25), lGp[1][1], T(0)));
+    const T leop = fma(T(-0.5), lGp[2][3], fma(T(0.333333333333333333333), lGp[2][2], T(0)));
+    const T leeu = fma(T(0.333333333333333333333), lGuv[1][3], fma(T(-0.333333333333333333333), lGuv[1][2], T(0)));
+    const T loeu = fma(T(-0.333333333333333333333), lGuv[0][2], fma(T(0.25), lGuv[0][1], T(0)));
+    const T loou = fma(T(0.333333333333333333333), lGuv[2][2], fma(T(-0.25), lGuv[2][1], T(0)));
+    const T leev = fma(T(0.333333333333333333333), lGuv[2][3], fma(T(-0.166666666666666666667), lGuv[2][2], T(0)));
+    const T leov = fma(T(-0.5), lGuv[0][3], fma(T(0.333333333333333333333), lGuv[0][2], T(0)));
+    const T loov = fma(T(0.333333333333333333333), lGuv[1][2], fma(T(-0.25), lGuv[1][1], T(0)));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(1, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(1, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-1, 2, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-1, -2, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+  }
+}
+
 // family C: 3 orbit representatives
 template <typename T, typename Load>
 __device__ __forceinline__ void af_sac_C(const Load& L, T pK, T uK, T vK, T Gp[3][4], T Guv[3][4]) {
@@ -725,5 +1004,52 @@ __device__ __forceinline__ void af_sac_C(const Load& L, T pK, T uK, T vK, T Gp[3
     Gp[2][2] = fma(T(-0.666666666666666666667), eop, Gp[2][2]);
     Guv[2][1] = fma(T(0.5), oou, Guv[2][1]);
     Guv[2][3] = fma(T(0.666666666666666666667), eev, Guv[2][3]);
+  }
+}
+
+// family C, transposed: lattice adjoints from output adjoints
+template <typename T, typename Scatter>
+__device__ __forceinline__ void af_sac_C_adj(const Scatter& S, const T lGp[3][4], const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
+  {  // orbit (+-0, +-1) half cells
+    const T leep = fma(T(-2.66666666666666666667), lGp[0][3], fma(T(2.0), lGp[0][1], T(0)));
+    const T leop = fma(T(1.33333333333333333333), lGp[2][2], fma(T(-1.0), lGp[2][0], T(0)));
+    const T leeu = fma(T(-1.33333333333333333333), lGuv[1][3], T(0));
+    const T leev = fma(T(-1.33333333333333333333), lGuv[2][3], fma(T(2.0), lGuv[2][1], T(0)));
+    const T leov = fma(T(1.33333333333333333333), lGuv[0][2], fma(T(-1.0), lGuv[0][0], T(0)));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(0, 1, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
+    S(0, -1, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+  }
+  {  // orbit (+-1, +-0) half cells
+    const T leep = fma(T(-2.66666666666666666667), lGp[0][3], fma(T(2.0), lGp[0][1], T(0)));
+    const T loep = fma(T(1.33333333333333333333), lGp[1][2], fma(T(-1.0), lGp[1][0], T(0)));
+    const T leeu = fma(T(-1.33333333333333333333), lGuv[1][3], fma(T(2.0), lGuv[1][1], T(0)));
+    const T loeu = fma(T(1.33333333333333333333), lGuv[0][2], fma(T(-1.0), lGuv[0][0], T(0)));
+    const T leev = fma(T(-1.33333333333333333333), lGuv[2][3], T(0));
+    lpK -= T(2) * leep;
+    luK -= T(2) * leeu;
+    lvK -= T(2) * leev;
+    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
+    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+  }
+  {  // orbit (+-1, +-1) half cells
+    const T leep = fma(T(1.33333333333333333333), lGp[0][3], T(0));
+    const T loep = fma(T(-0.666666666666666666667), lGp[1][2], T(0));
+    const T leop = fma(T(-0.666666666666666666667), lGp[2][2], T(0));
+    const T leeu = fma(T(0.666666666666666666667), lGuv[1][3], T(0));
+    const T loeu = fma(T(-0.666666666666666666667), lGuv[0][2], T(0));
+    const T loou = fma(T(0.5), lGuv[2][1], T(0));
+    const T leev = fma(T(0.666666666666666666667), lGuv[2][3], T(0));
+    const T leov = fma(T(-0.666666666666666666667), lGuv[0][2], T(0));
+    const T loov = fma(T(0.5), lGuv[1][1], T(0));
+    lpK -= T(4) * leep;
+    luK -= T(4) * leeu;
+    lvK -= T(4) * leev;
+    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
+    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
+    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
 }

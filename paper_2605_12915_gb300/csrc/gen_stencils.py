@@ -237,6 +237,73 @@ def emit_family(name, reps):
     return lines, nfma, nadd
 
 
+def emit_family_adjoint(name, reps):
+    """Transpose of emit_family: given the adjoints lGp, lGuv of the outputs,
+    scatter the adjoints of the lattice values through S(dx, dy, lp, lu, lv) and
+    accumulate those of the node's own values (deviation form) into lpK, luK, lvK."""
+    lines = []
+    lines.append("// family %s, transposed: lattice adjoints from output adjoints" % name)
+    lines.append("template <typename T, typename Scatter>")
+    lines.append("__device__ __forceinline__ void af_sac_%s_adj(const Scatter& S, const T lGp[3][4],"
+                 " const T lGuv[3][4], T& lpK, T& luK, T& lvK) {" % name)
+    for (a, b) in sorted(reps):
+        chans = reps[(a, b)]
+        lines.append("  {  // orbit (+-%d, +-%d) half cells" % (a, b))
+        members = sorted({(sx * a, sy * b) for sx in (1, -1) for sy in (1, -1)},
+                         key=lambda m: (-m[0], -m[1]))
+        lam = {}
+        for f in CH_IN:
+            for par in ((0, 0), (1, 0), (0, 1), (1, 1)):
+                terms = []
+                for oi, o in enumerate(CH_OUT):
+                    if (o, f) not in chans or PARITY[(o, f)] != par:
+                        continue
+                    src = "lGp" if f == "p" else "lGuv"
+                    for q in sorted(chans[(o, f)]):
+                        val = chans[(o, f)][q]
+                        if val == 0:
+                            continue
+                        terms.append((literal(val), "%s[%d][%d]" % (src, oi, q - 1)))
+                if terms:
+                    nm = {(0, 0): "ee", (1, 0): "oe", (0, 1): "eo", (1, 1): "oo"}[par] + f
+                    expr = "T(0)"
+                    for c, v in terms:
+                        expr = "fma(%s, %s, %s)" % (c, v, expr)
+                    lines.append("    const T l%s = %s;" % (nm, expr))
+                    lam[(f, par)] = "l" + nm
+        kname = {"p": "lpK", "u": "luK", "v": "lvK"}
+        for f in CH_IN:
+            if (f, (0, 0)) in lam:
+                lines.append("    %s -= T(%d) * %s;" % (kname[f], len(members), lam[(f, (0, 0))]))
+        for (dx, dy) in members:
+            sx = 1 if dx >= 0 else -1
+            sy = 1 if dy >= 0 else -1
+            vals = []
+            for f in CH_IN:
+                expr = []
+                for par, nm in lam_items(lam, f):
+                    sgn = (sx if par[0] else 1) * (sy if par[1] else 1)
+                    if len(members) == 2 and par != (0, 0):
+                        # two-member orbits: the one odd combination is n0 - n1
+                        sgn = 1 if (dx, dy) == members[0] else -1
+                    expr.append(("+" if sgn > 0 else "-") + " " + nm)
+                e = " ".join(expr) if expr else "+ T(0)"
+                vals.append("T(0) " + e)
+            lines.append("    S(%d, %d, %s, %s, %s);" % (dx, dy, vals[0], vals[1], vals[2]))
+        lines.append("  }")
+    lines.append("}")
+    lines.append("")
+    return lines
+
+
+def lam_items(lam, f):
+    out = []
+    for par in ((0, 0), (1, 0), (0, 1), (1, 1)):
+        if (f, par) in lam:
+            out.append((par, lam[(f, par)]))
+    return out
+
+
 def main(out_path):
     header = [
         "// GENERATED by gen_stencils.py -- do not edit.",
@@ -255,6 +322,7 @@ def main(out_path):
         reps = check_and_orbits(coef)
         lines, nfma, nadd = emit_family(name, reps)
         body += lines
+        body += emit_family_adjoint(name, reps)
         stats.append("//   %-2s: %3d multiply-adds, %3d adds" % (name, nfma, nadd))
     text = "\n".join(header + ["// operation counts per node:"] + stats + [""] + body)
     with open(out_path, "w") as f:
