@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--kernel-reps", type=int, default=20)
     p.add_argument("--fp64-steps", type=int, default=100,
                    help="steps of the FP64 comparison run (0: skip)")
+    p.add_argument("--adjoint-steps", type=int, default=5,
+                   help="adjoint steps timed against the forward step (0: skip)")
     return p.parse_args()
 
 
@@ -301,6 +303,8 @@ def main():
                     "note": "the path is issue/ALU bound; peak = 152 SMs x 128 FP32 lanes x SM clock"}}
     fp64 = fp64_compare(af, I, P, solver_state_after(af, P, args, stream), args, stream, torch) \
         if args.fp64_steps > 0 else None
+    adjoint = adjoint_cost(af, P, args, stream, torch, kstats["ms_per_launch"]) \
+        if args.adjoint_steps > 0 else None
     drift = (inv1[:4] - inv0[:4]) / np.array([inv0[0], inv0[0], inv0[0], inv0[3]])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -317,6 +321,7 @@ def main():
             "gpu_launches": kstats["launches_per_step"] * args.steps,
             "clocks": csum,
             "fp64": fp64,
+            "adjoint": adjoint,
             "conservation_drift": [float(x) for x in drift],
             "entropy_change": float(inv1[4] - inv0[4])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -327,6 +332,27 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def adjoint_cost(af, P, args, stream, torch, fwd_ms):
+    """Time of one discrete adjoint step (af_adjoint_step, device buffers, same
+    precision and workload) against one forward step."""
+    s = af.Solver(P.grid, P.gamma, P.state, precision=args.precision, stream=stream)
+    lam = torch.ones((16, P.grid.ny, P.grid.nx), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(lam)
+    s.adjoint(P.dt, lam, out)  # allocates the adjoint work planes
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.adjoint_steps):
+        s.adjoint(P.dt, lam, out)
+    e1.record(stream)
+    e1.synchronize()
+    s.close()
+    ms = e0.elapsed_time(e1) / args.adjoint_steps
+    return {"ms_per_step": ms, "forward_ms_per_step": fwd_ms, "ratio": ms / fwd_ms,
+            "note": "adjoint recomputes the step's intermediates with the unfused kernels and "
+                    "includes FP64 conversion of the adjoint state in and out"}
 
 
 def solver_state_after(af, P, args, stream):

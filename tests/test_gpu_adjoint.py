@@ -8,7 +8,10 @@ checkpointed differentiable rollout built on it.
   compared element by element with the GPU adjoint;
 * a 20-step rollout with checkpoints every 7 steps: the gradient of the final
   kinetic energy against central differences along seeded directions (KH
-  initial data), in FP64 and FP32.
+  initial data), in FP64 and FP32.  The KH data put convective feet exactly on
+  cell boundaries (v vanishes on grid columns), where the discrete map is only
+  piecewise smooth; a seeded 1e-4 smooth perturbation moves them off so that
+  central differences measure the derivative the adjoint computes.
 """
 import numpy as np
 import pytest
@@ -82,7 +85,7 @@ def _rollout_grad(P, n_steps, every, precision):
     xn = rollout(x0, P.grid, P.gamma, P.dt, n_steps, every, precision)
     J = kinetic_energy(xn, P.grid.h)
     J.backward()
-    return float(J), x0.grad.cpu().numpy()
+    return float(J.detach()), x0.grad.cpu().numpy()
 
 
 def _ke_after(P, x, n_steps, precision):
@@ -97,6 +100,8 @@ def _ke_after(P, x, n_steps, precision):
 def test_rollout_gradient_matches_finite_differences(precision, tol):
     pytest.importorskip("torch")
     P = I.kelvin_helmholtz(n=32)
+    Q = I.random_smooth(32, 32, seed=17, amp=0.05, flow=(0.0, 0.0), h=P.grid.h)
+    P.state = P.state + 2e-3 * (Q.state - np.mean(Q.state, axis=(1, 2), keepdims=True))
     n_steps, every = 20, 7
     J, g = _rollout_grad(P, n_steps, every, precision)
     rng = np.random.default_rng(3)
