@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--kernel-reps", type=int, default=20)
     p.add_argument("--fp64-steps", type=int, default=100,
                    help="steps of the FP64 comparison run (0: skip)")
+    p.add_argument("--ensemble", action="store_true",
+                   help="also measure the batched 256-grid vortex ensemble (200 steps)")
     p.add_argument("--adjoint-steps", type=int, default=5,
                    help="adjoint steps timed against the forward step (0: skip)")
     return p.parse_args()
@@ -305,6 +307,7 @@ def main():
         if args.fp64_steps > 0 else None
     adjoint = adjoint_cost(af, P, args, stream, torch, kstats["ms_per_launch"]) \
         if args.adjoint_steps > 0 else None
+    ensemble = ensemble_block(af, I, stream, torch) if args.ensemble else None
     drift = (inv1[:4] - inv0[:4]) / np.array([inv0[0], inv0[0], inv0[0], inv0[3]])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -322,6 +325,7 @@ def main():
             "clocks": csum,
             "fp64": fp64,
             "adjoint": adjoint,
+            "ensemble": ensemble,
             "conservation_drift": [float(x) for x in drift],
             "entropy_change": float(inv1[4] - inv0[4])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -332,6 +336,47 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def ensemble_block(af, I, stream, torch, n_problems=256, steps=200):
+    """Seeded ensemble of isentropic vortices on grids of 64^2..512^2 cells, FP32:
+    one batched, graph-captured launch per step against per-grid launches."""
+    specs = I.ensemble(n_problems, seed=0, n_steps=steps)
+    probs = [I.ensemble_member(sp) for sp in specs]
+    dts = [p.dt for p in probs]
+    cells = sum(p.grid.nx * p.grid.ny for p in probs)
+    b = af.Batch(probs, precision="fp32", stream=stream)
+    b.step(dts, 1)  # tunes the tile geometry
+    b.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(dts, steps)
+    e1.record(stream)
+    e1.synchronize()
+    b.sync()
+    ms_batch = e0.elapsed_time(e1)
+    geom, tune = b.info()
+    b.close()
+    solvers = [af.Solver(p.grid, p.gamma, p.state, precision="fp32", stream=stream) for p in probs]
+    for s, dt in zip(solvers, dts):
+        s.step(dt, 1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s, dt in zip(solvers, dts):
+        s.step(dt, steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for s in solvers:
+        s.sync()
+        s.close()
+    return {"problems": n_problems, "cells": cells, "steps": steps,
+            "batched": {"value": cells * steps / (ms_batch * 1e-3), "unit": UNIT, "ms": ms_batch,
+                        "tile_geometry": ["32x32/512", "24x16/256x2", "16x16/256x3"][geom],
+                        "tune_ms_per_step": tune},
+            "sequential": {"value": cells * steps / (ms_seq * 1e-3), "unit": UNIT, "ms": ms_seq},
+            "speedup": ms_seq / ms_batch}
 
 
 def adjoint_cost(af, P, args, stream, torch, fwd_ms):

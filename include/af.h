@@ -162,6 +162,38 @@ const char *af_status_string(af_status s);
 af_status af_step_noalloc(const af_grid *g, double gamma, double dt, af_variant var,
                           const af_state_f64 *in, const af_state_f64 *out, void *cuda_stream);
 
+/* ---- Batched ensembles ----------------------------------------------------
+ * Many independent grids (each with its own size, cell side, time step and
+ * state) advanced together: every step is one launch of the fused FP32 kernel
+ * over a table of the tiles of all grids, and the launches of an af_batch_step
+ * call are captured once in a CUDA graph (re-captured when n_steps changes).
+ * The first af_batch_step times the compiled tile geometries on the actual
+ * ensemble (states are snapshotted and restored around the trials) and keeps
+ * the fastest.  Per-grid results are bitwise those of af_step on a lone handle. */
+typedef struct af_batch af_batch;
+
+/* n grids; grids[k], states[k] as in af_init; prec must be AF_FP32 or
+ * AF_FP32_COMP.  On error *out is NULL. */
+af_status af_batch_init(af_batch **out, int32_t n, const af_grid *grids, double gamma,
+                        const af_state_f64 *states, af_memory where, af_precision prec,
+                        af_variant var, void *cuda_stream);
+
+/* n_steps steps of every grid k with time step dts[k] (host array of n).
+ * Asynchronous; returns a latched device error of an earlier call, if any. */
+af_status af_batch_step(af_batch *b, const double *dts, int32_t n_steps);
+
+/* Wait for the stream; the first latched device error of any grid. */
+af_status af_batch_sync(af_batch *b);
+
+/* State of grid k (as af_get_state). */
+af_status af_batch_get_state(af_batch *b, int32_t k, const af_state_f64 *out, af_memory where);
+
+/* The tile geometry chosen by the autotuner (index, -1 before the first step)
+ * and, if tune_ms is not NULL, the per-step time of each candidate (3 floats). */
+af_status af_batch_info(af_batch *b, int32_t *geometry, float *tune_ms);
+
+void af_batch_destroy(af_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,20 @@ def load():
         lib.af_adjoint_step.argtypes = [vp, d, ctypes.POINTER(AfState), ctypes.POINTER(AfState),
                                         ctypes.c_int]
         lib.af_adjoint_step.restype = ctypes.c_int
+        lib.af_batch_init.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(AfGrid), d,
+                                      ctypes.POINTER(AfState), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, vp]
+        lib.af_batch_init.restype = ctypes.c_int
+        lib.af_batch_step.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
+        lib.af_batch_step.restype = ctypes.c_int
+        lib.af_batch_sync.argtypes = [vp]
+        lib.af_batch_sync.restype = ctypes.c_int
+        lib.af_batch_get_state.argtypes = [vp, i32, ctypes.POINTER(AfState), ctypes.c_int]
+        lib.af_batch_get_state.restype = ctypes.c_int
+        lib.af_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+        lib.af_batch_info.restype = ctypes.c_int
+        lib.af_batch_destroy.argtypes = [vp]
+        lib.af_batch_destroy.restype = None
         lib.af_destroy.argtypes = [vp]
         lib.af_destroy.restype = None
         lib.af_status_string.argtypes = [ctypes.c_int]
@@ -241,6 +255,71 @@ class Solver:
     def close(self):
         if self.handle:
             af_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """An ensemble of independent grids stepped together (af_batch_*).
+
+    problems: sequence of objects with .grid, .gamma, .state (numpy (16, ny, nx)
+    float64 host arrays), as built by ``inputs``; all share gamma."""
+
+    def __init__(self, problems, precision="fp32", variant="tai", stream=None):
+        import numpy as np
+        n = len(problems)
+        self.n = n
+        self._states = [np.ascontiguousarray(p.state, dtype=np.float64) for p in problems]
+        grids = (AfGrid * n)()
+        states = (AfState * n)()
+        for k, p in enumerate(problems):
+            grids[k] = AfGrid(p.grid.nx, p.grid.ny, p.grid.h)
+            states[k] = _state_struct(self._states[k].ctypes.data, p.grid.nx * p.grid.ny)
+        self.shapes = [(p.grid.ny, p.grid.nx) for p in problems]
+        hnd = ctypes.c_void_p()
+        s = getattr(stream, "cuda_stream", stream)
+        rc = load().af_batch_init(ctypes.byref(hnd), n, grids, problems[0].gamma, states, AF_HOST,
+                                  PRECISIONS.get(precision, precision),
+                                  VARIANTS.get(variant, variant), ctypes.c_void_p(s) if s else None)
+        if rc != AF_OK:
+            raise AfError(rc, "af_batch_init")
+        self.handle = hnd.value
+
+    def step(self, dts, n_steps=1):
+        arr = (ctypes.c_double * self.n)(*[float(x) for x in dts])
+        rc = load().af_batch_step(ctypes.c_void_p(self.handle), arr, int(n_steps))
+        if rc != AF_OK:
+            raise AfError(rc, "af_batch_step")
+
+    def sync(self):
+        rc = load().af_batch_sync(ctypes.c_void_p(self.handle))
+        if rc != AF_OK:
+            raise AfError(rc, "af_batch_sync")
+
+    def state(self, k):
+        import numpy as np
+        out = np.empty((16,) + self.shapes[k])
+        st = _state_struct(out.ctypes.data, out.shape[1] * out.shape[2])
+        rc = load().af_batch_get_state(ctypes.c_void_p(self.handle), int(k), ctypes.byref(st),
+                                       AF_HOST)
+        if rc != AF_OK:
+            raise AfError(rc, "af_batch_get_state")
+        return out
+
+    def info(self):
+        g = ctypes.c_int32()
+        t = (ctypes.c_float * 3)()
+        load().af_batch_info(ctypes.c_void_p(self.handle), ctypes.byref(g), t)
+        return g.value, list(t)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().af_batch_destroy(ctypes.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):

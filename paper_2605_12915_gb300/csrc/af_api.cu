@@ -576,3 +576,261 @@ void af_destroy(af_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched ensembles: many independent grids advanced by one launch per step
+// (a tile table spanning all grids), the launches of a call captured once in a
+// CUDA graph; the tile geometry is chosen by timing the candidates.
+// ---------------------------------------------------------------------------
+struct af_batch {
+  int n;
+  af_handle** h;
+  cudaStream_t stream;
+  af_precision prec;
+  StepArgs<float>* h_args;  // pinned host copy [2][n]
+  StepArgs<float>* d_args;  // device [2][n]: parity p = the handles' current buffer
+  int4* d_tiles[N_BATCH_GEOMS];
+  int ntiles[N_BATCH_GEOMS];
+  int geom;                 // -1 until tuned
+  float tune_ms[N_BATCH_GEOMS];
+  cudaGraphExec_t graph;
+  int graph_steps, graph_parity;
+  void* snapshot;           // device copy of every state while tuning
+};
+
+namespace {
+
+af_status batch_launch(af_batch* b, int geom, int parity) {
+  const StepArgs<float>* args = b->d_args + (size_t)parity * b->n;
+  cudaError_t e = b->prec == AF_FP32_COMP
+                      ? launch_batch<true>(geom, b->stream, args, b->d_tiles[geom], b->ntiles[geom])
+                      : launch_batch<false>(geom, b->stream, args, b->d_tiles[geom],
+                                            b->ntiles[geom]);
+  return e == cudaSuccess ? AF_OK : AF_ERR_CUDA;
+}
+
+int batch_parity(const af_batch* b) { return b->h[0]->cur; }
+
+void batch_flip(af_batch* b, int n_steps) {
+  if (n_steps & 1)
+    for (int k = 0; k < b->n; ++k) b->h[k]->cur ^= 1;
+}
+
+size_t state_plane_bytes(const af_handle* h) { return (h->N * h->esize + 255) & ~(size_t)255; }
+
+af_status batch_snapshot(af_batch* b, bool restore) {
+  char* p = (char*)b->snapshot;
+  for (int k = 0; k < b->n; ++k) {
+    af_handle* h = b->h[k];
+    const size_t bytes = state_plane_bytes(h);
+    for (int q = 0; q < 20; ++q) {
+      void* live = h->state[h->cur][q];
+      if (cudaMemcpyAsync(restore ? live : (void*)p, restore ? (void*)p : live, bytes,
+                          cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+        return AF_ERR_CUDA;
+      p += bytes;
+    }
+  }
+  return AF_OK;
+}
+
+af_status batch_tune(af_batch* b) {
+  size_t total = 0;
+  for (int k = 0; k < b->n; ++k) total += 20 * state_plane_bytes(b->h[k]);
+  if (cudaMalloc(&b->snapshot, total) != cudaSuccess) {
+    b->snapshot = nullptr;
+    return AF_ERR_ALLOC;
+  }
+  af_status st = batch_snapshot(b, false);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int g = 0; g < N_BATCH_GEOMS && st == AF_OK; ++g) {
+    int parity = batch_parity(b);
+    st = batch_launch(b, g, parity);  // warm-up, attribute set-up
+    parity ^= 1;
+    cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < 2 && st == AF_OK; ++r, parity ^= 1) st = batch_launch(b, g, parity);
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->tune_ms[g] = ms / 2;
+    if (ms < best) {
+      best = ms;
+      b->geom = g;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == AF_OK) st = batch_snapshot(b, true);  // three steps per candidate: parity unchanged
+  for (int k = 0; k < b->n; ++k) cudaMemsetAsync(b->h[k]->d_flags, 0, sizeof(unsigned), b->stream);
+  cudaStreamSynchronize(b->stream);
+  cudaFree(b->snapshot);
+  b->snapshot = nullptr;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+af_status af_batch_init(af_batch** out, int32_t n, const af_grid* grids, double gamma,
+                        const af_state_f64* states, af_memory where, af_precision prec,
+                        af_variant var, void* cuda_stream) {
+  if (!out) return AF_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || !grids || !states || (prec != AF_FP32 && prec != AF_FP32_COMP)) return AF_ERR_ARG;
+  af_batch* b = new (std::nothrow) af_batch();
+  if (!b) return AF_ERR_ALLOC;
+  memset(b, 0, sizeof(*b));
+  b->n = n;
+  b->prec = prec;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->geom = -1;
+  b->h = new (std::nothrow) af_handle*[n]();
+  if (!b->h) {
+    delete b;
+    return AF_ERR_ALLOC;
+  }
+  for (int k = 0; k < n; ++k) {
+    af_status st = af_init(&b->h[k], &grids[k], gamma, &states[k], where, prec, var, cuda_stream);
+    if (st != AF_OK) {
+      af_batch_destroy(b);
+      return st;
+    }
+  }
+  // tile tables, largest grids first
+  int* order = new int[n];
+  for (int k = 0; k < n; ++k) order[k] = k;
+  for (int x = 1; x < n; ++x)
+    for (int y = x; y > 0 && b->h[order[y]]->N > b->h[order[y - 1]]->N; --y) {
+      int t = order[y];
+      order[y] = order[y - 1];
+      order[y - 1] = t;
+    }
+  bool ok = true;
+  for (int g = 0; g < N_BATCH_GEOMS && ok; ++g) {
+    const int tx = BATCH_GEOMS[g].tx, ty = BATCH_GEOMS[g].ty;
+    size_t cnt = 0;
+    for (int k = 0; k < n; ++k)
+      cnt += (size_t)((b->h[k]->nx + tx - 1) / tx) * ((b->h[k]->ny + ty - 1) / ty);
+    int4* tt = new int4[cnt];
+    size_t c = 0;
+    for (int o = 0; o < n; ++o) {
+      const int k = order[o];
+      for (int j0 = 0; j0 < b->h[k]->ny; j0 += ty)
+        for (int i0 = 0; i0 < b->h[k]->nx; i0 += tx) tt[c++] = make_int4(k, i0, j0, 0);
+    }
+    b->ntiles[g] = (int)cnt;
+    ok = cudaMalloc(&b->d_tiles[g], sizeof(int4) * cnt) == cudaSuccess &&
+         cudaMemcpy(b->d_tiles[g], tt, sizeof(int4) * cnt, cudaMemcpyHostToDevice) == cudaSuccess;
+    delete[] tt;
+  }
+  delete[] order;
+  ok = ok && cudaMallocHost(&b->h_args, sizeof(StepArgs<float>) * 2 * n) == cudaSuccess &&
+       cudaMalloc(&b->d_args, sizeof(StepArgs<float>) * 2 * n) == cudaSuccess;
+  if (!ok) {
+    af_batch_destroy(b);
+    return AF_ERR_ALLOC;
+  }
+  *out = b;
+  return AF_OK;
+}
+
+af_status af_batch_step(af_batch* b, const double* dts, int32_t n_steps) {
+  if (!b || !dts || n_steps < 0) return AF_ERR_ARG;
+  for (int k = 0; k < b->n; ++k) {
+    if (!(dts[k] > 0.0)) return AF_ERR_ARG;
+    if (b->h[k]->broken) return AF_ERR_STATE;
+    af_status prior = map_flags(*(volatile unsigned*)b->h[k]->h_flags);
+    if (prior != AF_OK) return prior;
+  }
+  if (n_steps == 0) return AF_OK;
+  DeviceGuard guard(b->h[0]->device);
+  // step arguments of both parities, with this call's time steps
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < b->n; ++k) {
+      af_handle* h = b->h[k];
+      const int cur = h->cur;
+      h->cur = p;
+      StepArgs<float> a = step_args<float>(h, dts[k]);
+      a.prefetch_wave = 0;
+      h->cur = cur;
+      b->h_args[(size_t)p * b->n + k] = a;
+    }
+  if (cudaMemcpyAsync(b->d_args, b->h_args, sizeof(StepArgs<float>) * 2 * b->n,
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return AF_ERR_CUDA;
+  if (b->geom < 0) {
+    af_status st = batch_tune(b);
+    if (st != AF_OK) return st;
+  }
+  const int parity = batch_parity(b);
+  if (!b->graph || b->graph_steps != n_steps || b->graph_parity != parity) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaGraph_t g;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return AF_ERR_CUDA;
+    int p = parity;
+    af_status st = AF_OK;
+    for (int s = 0; s < n_steps && st == AF_OK; ++s, p ^= 1) st = batch_launch(b, b->geom, p);
+    if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess || st != AF_OK) return AF_ERR_CUDA;
+    cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return AF_ERR_CUDA;
+    }
+    b->graph_steps = n_steps;
+    b->graph_parity = parity;
+  }
+  if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return AF_ERR_CUDA;
+  batch_flip(b, n_steps);
+  for (int k = 0; k < b->n; ++k)
+    cudaMemcpyAsync(b->h[k]->h_flags, b->h[k]->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                    b->stream);
+  return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA;
+}
+
+af_status af_batch_sync(af_batch* b) {
+  if (!b) return AF_ERR_ARG;
+  af_status first = AF_OK;
+  for (int k = 0; k < b->n; ++k) {
+    af_status st = af_sync(b->h[k]);
+    if (first == AF_OK) first = st;
+  }
+  return first;
+}
+
+af_status af_batch_get_state(af_batch* b, int32_t k, const af_state_f64* out, af_memory where) {
+  if (!b || k < 0 || k >= b->n) return AF_ERR_ARG;
+  return af_get_state(b->h[k], out, where);
+}
+
+af_status af_batch_info(af_batch* b, int32_t* geometry, float* tune_ms) {
+  if (!b || !geometry) return AF_ERR_ARG;
+  *geometry = b->geom;
+  if (tune_ms)
+    for (int g = 0; g < N_BATCH_GEOMS; ++g) tune_ms[g] = b->tune_ms[g];
+  return AF_OK;
+}
+
+void af_batch_destroy(af_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (int g = 0; g < N_BATCH_GEOMS; ++g)
+    if (b->d_tiles[g]) cudaFree(b->d_tiles[g]);
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->h_args) cudaFreeHost(b->h_args);
+  if (b->snapshot) cudaFree(b->snapshot);
+  if (b->h) {
+    for (int k = 0; k < b->n; ++k) af_destroy(b->h[k]);
+    delete[] b->h;
+  }
+  delete b;
+}
+
+}  // extern "C"

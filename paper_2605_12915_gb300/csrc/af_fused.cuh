@@ -38,6 +38,7 @@
 #ifndef AF_FUSED_MINB
 #define AF_FUSED_MINB 1
 #endif
+#define AF_FUSED_GEOMETRY_SET 1
 
 namespace af {
 
@@ -130,8 +131,12 @@ __device__ __forceinline__ int foot_axis(int o, float d, float l[3]) {
   return (int)fl;
 }
 
+// One tile of the step: the CTA owns cells [i0, i0+TX) x [j0, j0+TY) of the grid
+// described by `a`; (pi0, pj0), if pi0 >= 0, is a tile of the same grid whose
+// rows are prefetched into L2 for a later CTA.
 template <int TX, int TY, int NT, bool COMP>
-__global__ void __launch_bounds__(NT, AF_FUSED_MINB) k_fused_step(StepArgs<float> a) {
+__device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int j0, int pi0,
+                                           int pj0) {
   using G = FusedGeom<TX, TY>;
   constexpr int CW = G::CW, CH = G::CH, DCW = G::DCW, PW = G::PW;
   constexpr int WPL = G::WPL, DPL = G::DPL, PPL = G::PPL;
@@ -141,17 +146,12 @@ __global__ void __launch_bounds__(NT, AF_FUSED_MINB) k_fused_step(StepArgs<float
   float* FLX = reinterpret_cast<float*>(smem4);  // fluxes overwrite W in phase 4
 
   const int nx = a.nx, ny = a.ny;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const Gas<float> gas = a.gas;
   unsigned bad = 0;
 
-  // ---- L2 prefetch of the tile that runs one wave later on this GPU ---------
-  // (linear block id + wave size): its phase 0 then reads from L2, not DRAM.
+  // ---- L2 prefetch of a later CTA's tile -------------------------------------
   {
-    const int wave = a.prefetch_wave;
-    const int nxt = blockIdx.y * gridDim.x + blockIdx.x + wave;
-    if (wave > 0 && nxt < gridDim.x * gridDim.y && (nx & 3) == 0) {
-      const int pi0 = (nxt % gridDim.x) * TX, pj0 = (nxt / gridDim.x) * TY;
+    if (pi0 >= 0 && (nx & 3) == 0) {
       if (pi0 >= 4 && pj0 >= 2 && pi0 + TX + 4 <= nx && pj0 + CH - 2 <= ny) {
         constexpr int NPF = 20 * CH;  // one 16-byte-aligned row segment per plane and row
         for (int t = threadIdx.x; t < NPF; t += NT) {
@@ -490,12 +490,34 @@ __global__ void __launch_bounds__(NT, AF_FUSED_MINB) k_fused_step(StepArgs<float
   if (bad) atomicOr(a.flags, bad);
 }
 
+template <int TX, int TY, int NT, int MINB, bool COMP>
+__global__ void __launch_bounds__(NT, MINB)
+    k_fused_step(const __grid_constant__ StepArgs<float> a) {
+  // prefetch into L2 the tile of the CTA that starts one wave later
+  int pi0 = -1, pj0 = -1;
+  const int nxt = blockIdx.y * gridDim.x + blockIdx.x + a.prefetch_wave;
+  if (a.prefetch_wave > 0 && nxt < gridDim.x * gridDim.y) {
+    pi0 = (nxt % gridDim.x) * TX;
+    pj0 = (nxt / gridDim.x) * TY;
+  }
+  fused_tile<TX, TY, NT, COMP>(a, blockIdx.x * TX, blockIdx.y * TY, pi0, pj0);
+}
+
+// Batched form: one CTA per entry (grid, i0, j0, -) of a tile table spanning
+// many independent grids; args[grid] describes each grid's step.
+template <int TX, int TY, int NT, int MINB, bool COMP>
+__global__ void __launch_bounds__(NT, MINB)
+    k_fused_step_batch(const StepArgs<float>* __restrict__ args, const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];
+  fused_tile<TX, TY, NT, COMP>(args[t.x], t.y, t.z, -1, -1);
+}
+
 constexpr int FUSED_TX = AF_FUSED_TX, FUSED_TY = AF_FUSED_TY, FUSED_NT = AF_FUSED_NT;
 
 template <bool COMP>
 inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a) {
   using G = FusedGeom<FUSED_TX, FUSED_TY>;
-  auto kern = k_fused_step<FUSED_TX, FUSED_TY, FUSED_NT, COMP>;
+  auto kern = k_fused_step<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -506,6 +528,40 @@ inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a) {
   dim3 grd((a.nx + FUSED_TX - 1) / FUSED_TX, (a.ny + FUSED_TY - 1) / FUSED_TY);
   kern<<<grd, FUSED_NT, G::SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+// Tile geometries available to the batched launch (the autotuner picks one).
+struct BatchGeometry {
+  int tx, ty, nt, minb;
+};
+constexpr int N_BATCH_GEOMS = 3;
+constexpr BatchGeometry BATCH_GEOMS[N_BATCH_GEOMS] = {{32, 32, 512, 1}, {24, 16, 256, 2},
+                                                      {16, 16, 256, 3}};
+
+template <int TX, int TY, int NT, int MINB, bool COMP>
+inline cudaError_t launch_batch_geom(cudaStream_t s, const StepArgs<float>* args,
+                                     const int4* tiles, int ntiles) {
+  using G = FusedGeom<TX, TY>;
+  auto kern = k_fused_step_batch<TX, TY, NT, MINB, COMP>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<ntiles, NT, G::SMEM, s>>>(args, tiles);
+  return cudaGetLastError();
+}
+
+template <bool COMP>
+inline cudaError_t launch_batch(int geom, cudaStream_t s, const StepArgs<float>* args,
+                                const int4* tiles, int ntiles) {
+  switch (geom) {
+    case 0: return launch_batch_geom<32, 32, 512, 1, COMP>(s, args, tiles, ntiles);
+    case 1: return launch_batch_geom<24, 16, 256, 2, COMP>(s, args, tiles, ntiles);
+    default: return launch_batch_geom<16, 16, 256, 3, COMP>(s, args, tiles, ntiles);
+  }
 }
 
 }  // namespace af
