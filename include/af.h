@@ -173,7 +173,9 @@ af_status af_step_noalloc(const af_grid *g, double gamma, double dt, af_variant 
 typedef struct af_batch af_batch;
 
 /* n grids; grids[k], states[k] as in af_init; prec must be AF_FP32 or
- * AF_FP32_COMP.  On error *out is NULL. */
+ * AF_FP32_COMP.  cuda_stream NULL: the batch creates (and later destroys) a
+ * private non-blocking stream, since the legacy stream cannot be captured into
+ * a graph.  On error *out is NULL. */
 af_status af_batch_init(af_batch **out, int32_t n, const af_grid *grids, double gamma,
                         const af_state_f64 *states, af_memory where, af_precision prec,
                         af_variant var, void *cuda_stream);

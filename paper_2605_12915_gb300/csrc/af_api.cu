@@ -596,6 +596,7 @@ struct af_batch {
   cudaGraphExec_t graph;
   int graph_steps, graph_parity;
   void* snapshot;           // device copy of every state while tuning
+  int own_stream;           // the batch created its stream (the legacy stream cannot be captured)
 };
 
 namespace {
@@ -689,13 +690,21 @@ af_status af_batch_init(af_batch** out, int32_t n, const af_grid* grids, double 
   b->prec = prec;
   b->stream = (cudaStream_t)cuda_stream;
   b->geom = -1;
+  if (!b->stream) {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return AF_ERR_CUDA;
+    }
+    b->own_stream = 1;
+  }
   b->h = new (std::nothrow) af_handle*[n]();
   if (!b->h) {
     delete b;
     return AF_ERR_ALLOC;
   }
   for (int k = 0; k < n; ++k) {
-    af_status st = af_init(&b->h[k], &grids[k], gamma, &states[k], where, prec, var, cuda_stream);
+    af_status st = af_init(&b->h[k], &grids[k], gamma, &states[k], where, prec, var, b->stream);
     if (st != AF_OK) {
       af_batch_destroy(b);
       return st;
@@ -772,15 +781,22 @@ af_status af_batch_step(af_batch* b, const double* dts, int32_t n_steps) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     cudaGraph_t g;
-    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
       return AF_ERR_CUDA;
+    }
     int p = parity;
     af_status st = AF_OK;
     for (int s = 0; s < n_steps && st == AF_OK; ++s, p ^= 1) st = batch_launch(b, b->geom, p);
-    if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess || st != AF_OK) return AF_ERR_CUDA;
-    cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || st != AF_OK) {
+      cudaGetLastError();
+      return AF_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
+      cudaGetLastError();
       b->graph = nullptr;
       return AF_ERR_CUDA;
     }
@@ -830,6 +846,7 @@ void af_batch_destroy(af_batch* b) {
     for (int k = 0; k < b->n; ++k) af_destroy(b->h[k]);
     delete[] b->h;
   }
+  if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
 }
 
