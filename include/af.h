@@ -40,7 +40,9 @@ typedef enum {
   AF_ERR_CFL = 4,         /* c dt / h > 1/2 at a node, or a convective foot beyond one cell */
   AF_ERR_NONPHYSICAL = 5, /* rho <= 0 or p <= 0 where a sound speed is needed */
   AF_ERR_NONFINITE = 6,   /* NaN or Inf produced */
-  AF_ERR_STATE = 7        /* handle unusable (a previous CUDA error) */
+  AF_ERR_STATE = 7,       /* handle unusable (a previous CUDA error) */
+  AF_ERR_TIMEOUT = 8      /* a kernel's bounded wait for its own asynchronous copies ran
+                             out; the kernel stopped early and the step's result is invalid */
 } af_status;
 
 typedef enum {

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "../../include/af.h"
@@ -41,12 +42,16 @@ struct af_handle {
   int broken;
   int fused;             // 1: fused single-pass kernel for the FP32 modes
   int prefetch_wave;     // resident CTAs of the fused kernel (one wave)
+  int pipe_ctas;         // CTAs of the persistent pipelined fused kernel (0: off)
+  TileMaps* tmaps;       // tensor maps of the input planes of state[0], state[1]
+  int tma;               // 1: the pipelined kernel stages interior tiles by tensor copies
   void* adj_arena;       // adjoint planes (lazy): lin 16, lout 16, lwc 4, linc 24, lhalf 12, lfull 12
 };
 
 namespace {
 
 af_status map_flags(unsigned f) {
+  if (f & FLAG_TIMEOUT) return AF_ERR_TIMEOUT;
   if (f & FLAG_NONPHYSICAL) return AF_ERR_NONPHYSICAL;
   if (f & FLAG_NONFINITE) return AF_ERR_NONFINITE;
   if (f & (FLAG_CFL | FLAG_REACH)) return AF_ERR_CFL;
@@ -187,11 +192,15 @@ void launch_step(af_handle* h, double dt) {
   switch (h->prec) {
     case AF_FP64: launch_ref_step<double, false>(h, dt); break;
     case AF_FP32:
-      if (h->fused) launch_fused_step<false>(h->stream, step_args<float>(h, dt));
+      if (h->fused)
+        launch_fused_step<false>(h->stream, step_args<float>(h, dt), h->pipe_ctas > 0,
+                                 h->pipe_ctas, h->tma ? &h->tmaps[h->cur] : nullptr);
       else launch_ref_step<float, false>(h, dt);
       break;
     case AF_FP32_COMP:
-      if (h->fused) launch_fused_step<true>(h->stream, step_args<float>(h, dt));
+      if (h->fused)
+        launch_fused_step<true>(h->stream, step_args<float>(h, dt), h->pipe_ctas > 0,
+                                h->pipe_ctas, h->tma ? &h->tmaps[h->cur] : nullptr);
       else launch_ref_step<float, true>(h, dt);
       break;
   }
@@ -345,6 +354,7 @@ const char* af_status_string(af_status s) {
     case AF_ERR_NONPHYSICAL: return "non-positive density or pressure";
     case AF_ERR_NONFINITE: return "non-finite value in the state";
     case AF_ERR_STATE: return "handle unusable after a CUDA error";
+    case AF_ERR_TIMEOUT: return "a device-side wait for asynchronous copies timed out";
   }
   return "unknown status";
 }
@@ -385,6 +395,12 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     const char* pf = getenv("AF_PREFETCH");
     h->prefetch_wave = (pf && pf[0] == '0') ? 0 : sms * AF_FUSED_MINB;
+    // persistent pipelined fused kernel on one wave of CTAs; AF_PIPE=0 selects
+    // the one-CTA-per-tile kernel (same arithmetic), AF_PIPE=n > 0 caps the
+    // persistent grid at n CTAs
+    const char* pp = getenv("AF_PIPE");
+    const int cap = pp ? atoi(pp) : 0;
+    h->pipe_ctas = !pp ? sms * AF_FUSED_MINB : (cap > 0 ? std::min(cap, sms * AF_FUSED_MINB) : 0);
   }
   // 2 x 20 state planes + 48 scratch planes, each padded to 256 bytes
   size_t plane = (h->N * h->esize + 255) & ~(size_t)255;
@@ -406,6 +422,21 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
   if (!ok) {
     af_destroy(h);
     return AF_ERR_ALLOC;
+  }
+  if (prec != AF_FP64 && h->pipe_ctas > 0) {
+    // tensor maps of both state buffers for the pipelined kernel; AF_TMA=0 (or a
+    // driver without the encoder) stages every tile by cp.async instead
+    const char* tv = getenv("AF_TMA");
+    h->tmaps = new (std::nothrow) TileMaps[2];
+    bool enc = h->tmaps && !(tv && tv[0] == '0');
+    for (int b = 0; b < 2 && enc; ++b) {
+      StepArgs<float> a = {};
+      a.in = planes_of<float>(h, b);
+      a.nx = h->nx;
+      a.ny = h->ny;
+      enc = pipe_eligible(a) && encode_tile_maps(a, &h->tmaps[b]);
+    }
+    h->tma = enc ? 1 : 0;
   }
   if (prec == AF_FP32_COMP || prec == AF_FP32) {
     // zero the lo planes once (unused in AF_FP32)
@@ -572,6 +603,7 @@ void af_destroy(af_handle* h) {
   if (h->d_red) cudaFree(h->d_red);
   if (h->adj_arena) cudaFree(h->adj_arena);
   if (h->h_red) cudaFreeHost(h->h_red);
+  delete[] h->tmaps;
   delete h;
 }
 

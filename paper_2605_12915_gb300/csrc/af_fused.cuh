@@ -21,6 +21,8 @@
 // flagged, so every shared-memory access stays in bounds whatever the data.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the maps are encoded on the host)
+
 #include "af_common.cuh"
 #include "af_ref_kernels.cuh"
 
@@ -56,6 +58,13 @@ struct FusedGeom {
   static constexpr size_t W_BYTES = sizeof(float4) * 4 * WPL;
   static constexpr size_t DS_BYTES = sizeof(float) * 12 * DPL;  // one duration
   static constexpr size_t SMEM = W_BYTES + 2 * DS_BYTES;
+  // staged raw input of the pipelined kernel (in the D region): 20 planes
+  // (points [f][k], averages, lo words) of rows [j0-2, j0+TY+4) and cells
+  // [i0-4, i0+TX+4), row stride SW (16-byte rows)
+  // (plane stride SPL rounded up to 128 bytes for the tensor copies)
+  static constexpr int SW = TX + 8, SPL = (CH * SW + 31) / 32 * 32;
+  static constexpr bool STAGE_FITS = 20 * SPL * sizeof(float) <= 2 * DS_BYTES;
+  static constexpr size_t SMEM_PIPE = SMEM + 16;  // + the staging mbarrier
   static_assert(4 * NE * sizeof(float) <= W_BYTES, "fluxes alias W");
   static_assert(3 * PPL * sizeof(float4) <= DS_BYTES, "points of one duration alias its increments");
   static_assert(8 * WPL * sizeof(float) <= 2 * DS_BYTES, "averages wait in the D region");
@@ -131,12 +140,106 @@ __device__ __forceinline__ int foot_axis(int o, float d, float l[3]) {
   return (int)fl;
 }
 
-// One tile of the step: the CTA owns cells [i0, i0+TX) x [j0, j0+TY) of the grid
-// described by `a`; (pi0, pj0), if pi0 >= 0, is a tile of the same grid whose
-// rows are prefetched into L2 for a later CTA.
+// index in [-n, 2n) wrapped into [0, n)
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Tensor maps of the 20 input planes of one state buffer, each with the staging
+// box (SW x CH floats) of FusedGeom: [0,12) points [f][k], [12,16) averages,
+// [16,20) lo words.
+struct TileMaps {
+  CUtensorMap m[20];
+};
+
+// State of the staging pipeline of one CTA.
+struct PipeCtx {
+  const TileMaps* tm;  // null: every tile is staged by cp.async
+  unsigned bar;        // shared address of the staging mbarrier
+  unsigned phase;      // tensor stagings completed so far
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Waits for the completion of phase `parity` of the mbarrier at `bar`; gives up
+// (false) after about 50 ms or 2^22 polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 50000000ull) return false;
+  }
+  return false;
+}
+
+// A tile whose staging box lies inside the grid is staged by tensor copies (the
+// tensor unit would fill the periodic wrap with zeros).
+template <int TX, int TY>
+__device__ __forceinline__ bool box_inside(int nx, int ny, int i0, int j0) {
+  return i0 >= 4 && j0 >= 2 && i0 + TX + 4 <= nx && j0 + TY + 4 <= ny;
+}
+
+// Starts the asynchronous copy of the raw input of tile (i0, j0) into the
+// staging layout of FusedGeom at S: 20 (16 without lo words) 2D tensor copies
+// issued by thread 0 that complete on the mbarrier, or, for tiles on the
+// periodic boundary, 16-byte cp.async copies (one commit group).  Needs nx a
+// multiple of 4, 16-byte aligned planes, nx >= TX + 8 and ny >= TY + 6 (one
+// periodic wrap at most); a quad of cells never straddles the wrap since i0 - 4
+// and nx are multiples of 4.
 template <int TX, int TY, int NT, bool COMP>
-__device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int j0, int pi0,
-                                           int pj0) {
+__device__ __forceinline__ void issue_tile_async(const StepArgs<float>& a, const PipeCtx& pc,
+                                                 int i0, int j0, float* S) {
+  using G = FusedGeom<TX, TY>;
+  static_assert(G::STAGE_FITS, "the staged tile fits the D region");
+  constexpr int QW = G::SW / 4, CH = G::CH, NPL = COMP ? 20 : 16;
+  const unsigned sbase = smem_addr(S);
+  if (pc.tm && box_inside<TX, TY>(a.nx, a.ny, i0, j0)) {
+    if (threadIdx.x == 0) {
+      // the region was last read by generic loads of every thread (ordered by
+      // the barrier before this call)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(pc.bar),
+                   "r"((unsigned)(NPL * CH * G::SW * sizeof(float)))
+                   : "memory");
+#pragma unroll 1
+      for (int p = 0; p < NPL; ++p)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(sbase + 4u * (unsigned)(p * G::SPL)),
+            "l"(&pc.tm->m[p]), "r"(i0 - 4), "r"(j0 - 2), "r"(pc.bar)
+            : "memory");
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < NPL * CH * QW; t += NT) {
+    const int m = t % QW, r = (t / QW) % CH, pl = t / (QW * CH);
+    const float* base = pl < 12 ? a.in.pt[pl >> 2][pl & 3]
+                      : pl < 16 ? a.in.avg[pl - 12] : a.in.lo[pl - 16];
+    const size_t id = (size_t)wrap1(j0 - 2 + r, a.ny) * a.nx + wrap1(i0 - 4 + 4 * m, a.nx);
+    const unsigned dst = sbase + 4u * (unsigned)(pl * G::SPL + r * G::SW + 4 * m);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(base + id)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One tile of the step: the CTA owns cells [i0, i0+TX) x [j0, j0+TY) of the grid
+// described by `a`.  (pi0, pj0), if pi0 >= 0, is a later tile of the same grid:
+// its rows are prefetched into L2 when `pf` is set, and with PIPE its raw input
+// is copied asynchronously into the D region once this tile no longer needs it.
+// With PIPE this tile's own input is already on its way there
+// (issue_tile_async); false means the wait for it timed out (flagged).
+template <int TX, int TY, int NT, bool COMP, bool PIPE>
+__device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc, int i0, int j0,
+                                           int pi0, int pj0, bool pf) {
   using G = FusedGeom<TX, TY>;
   constexpr int CW = G::CW, CH = G::CH, DCW = G::DCW, PW = G::PW;
   constexpr int WPL = G::WPL, DPL = G::DPL, PPL = G::PPL;
@@ -149,9 +252,18 @@ __device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int
   const Gas<float> gas = a.gas;
   unsigned bad = 0;
 
-  // ---- L2 prefetch of a later CTA's tile -------------------------------------
-  {
-    if (pi0 >= 0 && (nx & 3) == 0) {
+  // ---- L2 prefetch of a later tile --------------------------------------------
+  if (PIPE && pc.tm) {
+    if (pf && pi0 >= 0 && threadIdx.x == 0 && box_inside<TX, TY>(nx, ny, pi0, pj0)) {
+#pragma unroll 1
+      for (int p = 0; p < (COMP ? 20 : 16); ++p)
+        asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                         &pc.tm->m[p]),
+                     "r"(pi0 - 4), "r"(pj0 - 2)
+                     : "memory");
+    }
+  } else {
+    if (pf && pi0 >= 0 && (nx & 3) == 0) {
       if (pi0 >= 4 && pj0 >= 2 && pi0 + TX + 4 <= nx && pj0 + CH - 2 <= ny) {
         constexpr int NPF = 20 * CH;  // one 16-byte-aligned row segment per plane and row
         for (int t = threadIdx.x; t < NPF; t += NT) {
@@ -170,10 +282,32 @@ __device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int
   }
 
   // ---- phase 0: every global load of the step, cells [i0-2, i0+TX+4)^2 ------
-  // Interior tiles read 16-byte quads of cells [i0-4, i0+TX+4) per row (rows are
-  // 16-byte aligned when nx is a multiple of 4); tiles touching the periodic
-  // boundary read cell by cell with wrapped indices.
-  {
+  // PIPE: the input is staged in D already; wait for it and build the point
+  // families of W from the staged planes (the averages stay staged for phase 1).
+  // Otherwise interior tiles read 16-byte quads of cells [i0-4, i0+TX+4) per
+  // row (rows are 16-byte aligned when nx is a multiple of 4), and tiles
+  // touching the periodic boundary read cell by cell with wrapped indices.
+  if constexpr (PIPE) {
+    if (pc.tm && box_inside<TX, TY>(nx, ny, i0, j0)) {
+      const bool late = !mbar_wait_bounded(pc.bar, pc.phase & 1u);
+      if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+        mbar_wait_bounded(pc.bar, pc.phase & 1u);
+        return false;
+      }
+      ++pc.phase;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    for (int t = threadIdx.x; t < CW * CH; t += NT) {
+      const int cx = t % CW, cy = t / CW;
+      const float* S = D + cy * G::SW + cx + 2;
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        W[f * WPL + t] = make_float4(S[(4 * f) * G::SPL], S[(4 * f + 1) * G::SPL],
+                                     S[(4 * f + 2) * G::SPL], S[(4 * f + 3) * G::SPL]);
+    }
+  } else {
     const bool interior = i0 >= 4 && j0 >= 2 && i0 + TX + 4 <= nx && j0 + CH - 2 <= ny &&
                           (nx & 3) == 0;
     if (interior) {
@@ -230,14 +364,17 @@ __device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int
 
   // ---- phase 1: centre recovery of cells [i0-2, i0+TX+3) (Eq. center-node) ----
   // deviation form U_c = Ubar + 1/16 sum_corners (Ubar - U_V) + 1/4 sum_edges (Ubar - U_E)
+  // averages of W cell (cx, cy): plane k at D[AB + k APL + cy ARS + cx + AOF]
+  constexpr int APL = PIPE ? G::SPL : WPL, ARS = PIPE ? G::SW : CW, AOF = PIPE ? 2 : 0;
+  constexpr int AB = PIPE ? 12 * G::SPL : 0;
   for (int t = threadIdx.x; t < (CW - 1) * (CH - 1); t += NT) {
     const int cx = t % (CW - 1), cy = t / (CW - 1);
-    const int c = cy * CW + cx;
+    const int c = cy * CW + cx, ca = AB + cy * ARS + cx + AOF;
     float ub[4], lo[4], sc[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f}, uc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      ub[k] = D[k * WPL + c];
-      lo[k] = COMP ? D[(4 + k) * WPL + c] : 0.f;
+      ub[k] = D[ca + k * APL];
+      lo[k] = COMP ? D[ca + (4 + k) * APL] : 0.f;
     }
     const float4 corners[4] = {W[c], W[c + 1], W[c + CW], W[c + CW + 1]};
     const float4 edges[4] = {W[2 * WPL + c], W[2 * WPL + c + CW], W[WPL + c], W[WPL + c + 1]};
@@ -411,6 +548,21 @@ __device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int
   // ex in [0, TX), ey in [0, TY].  Computed into registers, then stored over W.
   constexpr int NVE = G::NVE, NE = G::NE;
   constexpr int PERE = (NE + NT - 1) / NT;
+  // the owned averages (and lo words) at t^n, loaded while the fluxes are formed
+  constexpr int PERC = (TX * TY + NT - 1) / NT;
+  float hv[PERC][4], lv[PERC][4];
+#pragma unroll
+  for (int k = 0; k < PERC; ++k) {
+    const int t = threadIdx.x + k * NT;
+    const int gi = i0 + t % TX, gj = j0 + t / TX;
+    const bool own = t < TX * TY && gi < nx && gj < ny;
+    const size_t id = own ? (size_t)gj * nx + gi : 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      hv[k][q] = own ? __ldg(a.in.avg[q] + id) : 0.f;
+      lv[k][q] = (COMP && own) ? __ldg(a.in.lo[q] + id) : 0.f;
+    }
+  }
   float flux[PERE][4];
   const float lam = a.dt / (36.f * a.h);
 #pragma unroll
@@ -455,7 +607,10 @@ __device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int
 #pragma unroll
     for (int q = 0; q < 4; ++q) flux[k][q] = lam * F[q];
   }
-  __syncthreads();  // W is dead from here
+  __syncthreads();  // W and D are dead from here
+  if constexpr (PIPE) {
+    if (pi0 >= 0) issue_tile_async<TX, TY, NT, COMP>(a, pc, pi0, pj0, D);
+  }
 #pragma unroll
   for (int k = 0; k < PERE; ++k) {
     const int t = threadIdx.x + k * NT;
@@ -464,10 +619,12 @@ __device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int
     for (int q = 0; q < 4; ++q) FLX[q * NE + t] = flux[k][q];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < TX * TY; t += NT) {
+#pragma unroll
+  for (int k = 0; k < PERC; ++k) {
+    const int t = threadIdx.x + k * NT;
     const int cx = t % TX, cy = t / TX;
     const int gi = i0 + cx, gj = j0 + cy;
-    if (gi >= nx || gj >= ny) continue;
+    if (t >= TX * TY || gi >= nx || gj >= ny) continue;
     const size_t id = (size_t)gj * nx + gi;
     const int fl = cy * PW + cx, fr = fl + 1;         // vertical edges x_i, x_{i+1}
     const int gb = NVE + cy * TX + cx, gt = gb + TX;  // horizontal edges y_j, y_{j+1}
@@ -475,19 +632,20 @@ __device__ __forceinline__ void fused_tile(const StepArgs<float>& a, int i0, int
     for (int q = 0; q < 4; ++q) {
       const float* Fq = FLX + q * NE;
       if (COMP) {
-        float hi = __ldg(a.in.avg[q] + id), lo = __ldg(a.in.lo[q] + id);
+        float hi = hv[k][q], lo = lv[k][q];
         comp_update(hi, lo, Fq[fl], Fq[fr], Fq[gb], Fq[gt]);
         a.out.avg[q][id] = hi;
         a.out.lo[q][id] = lo;
         if (!isfinite(hi)) bad |= FLAG_NONFINITE;
       } else {
-        const float v = __ldg(a.in.avg[q] + id) - (Fq[fr] - Fq[fl]) - (Fq[gt] - Fq[gb]);
+        const float v = hv[k][q] - (Fq[fr] - Fq[fl]) - (Fq[gt] - Fq[gb]);
         a.out.avg[q][id] = v;
         if (!isfinite(v)) bad |= FLAG_NONFINITE;
       }
     }
   }
   if (bad) atomicOr(a.flags, bad);
+  return true;
 }
 
 template <int TX, int TY, int NT, int MINB, bool COMP>
@@ -500,7 +658,45 @@ __global__ void __launch_bounds__(NT, MINB)
     pi0 = (nxt % gridDim.x) * TX;
     pj0 = (nxt / gridDim.x) * TY;
   }
-  fused_tile<TX, TY, NT, COMP>(a, blockIdx.x * TX, blockIdx.y * TY, pi0, pj0);
+  PipeCtx none = {nullptr, 0u, 0u};
+  fused_tile<TX, TY, NT, COMP, false>(a, none, blockIdx.x * TX, blockIdx.y * TY, pi0, pj0,
+                                      pi0 >= 0);
+}
+
+// Persistent pipelined form: CTA b steps through tiles b, b + G, b + 2G, ...
+// (G = gridDim.x, row-major tile order).  The raw input of its next tile is
+// prefetched into L2 at the start of a tile and copied into shared memory
+// (tensor copies when `use_tma` and the box lies inside the grid, else
+// cp.async) while the current tile stores its fluxes and averages.  Requires
+// the conditions of issue_tile_async.
+template <int TX, int TY, int NT, int MINB, bool COMP>
+__global__ void __launch_bounds__(NT, MINB)
+    k_fused_step_pipe(const __grid_constant__ StepArgs<float> a,
+                      const __grid_constant__ TileMaps tm, int use_tma) {
+  using G = FusedGeom<TX, TY>;
+  extern __shared__ __align__(16) float4 smem4[];
+  float* S = reinterpret_cast<float*>(smem4 + 4 * G::WPL);
+  PipeCtx pc;
+  // tensor copies want 128-byte aligned destinations
+  pc.tm = (use_tma && G::W_BYTES % 128 == 0 && (smem_addr(smem4) & 127u) == 0) ? &tm : nullptr;
+  pc.bar = smem_addr(reinterpret_cast<char*>(smem4) + G::SMEM);
+  pc.phase = 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pc.bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int tcols = (a.nx + TX - 1) / TX, ntiles = tcols * ((a.ny + TY - 1) / TY);
+  int tile = blockIdx.x;
+  if (tile < ntiles)
+    issue_tile_async<TX, TY, NT, COMP>(a, pc, (tile % tcols) * TX, (tile / tcols) * TY, S);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    const int pi0 = nxt < ntiles ? (nxt % tcols) * TX : -1, pj0 = (nxt / tcols) * TY;
+    if (!fused_tile<TX, TY, NT, COMP, true>(a, pc, (tile % tcols) * TX, (tile / tcols) * TY, pi0,
+                                            pj0, a.prefetch_wave > 0))
+      break;
+  }
 }
 
 // Batched form: one CTA per entry (grid, i0, j0, -) of a tile table spanning
@@ -509,14 +705,79 @@ template <int TX, int TY, int NT, int MINB, bool COMP>
 __global__ void __launch_bounds__(NT, MINB)
     k_fused_step_batch(const StepArgs<float>* __restrict__ args, const int4* __restrict__ tiles) {
   const int4 t = tiles[blockIdx.x];
-  fused_tile<TX, TY, NT, COMP>(args[t.x], t.y, t.z, -1, -1);
+  PipeCtx none = {nullptr, 0u, 0u};
+  fused_tile<TX, TY, NT, COMP, false>(args[t.x], none, t.y, t.z, -1, -1, false);
 }
 
 constexpr int FUSED_TX = AF_FUSED_TX, FUSED_TY = AF_FUSED_TY, FUSED_NT = AF_FUSED_NT;
 
-template <bool COMP>
-inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a) {
+// The pipelined kernel's conditions on the grid and the input planes.
+inline bool pipe_eligible(const StepArgs<float>& a) {
+  if ((a.nx & 3) != 0 || a.nx < FUSED_TX + 8 || a.ny < FUSED_TY + 6) return false;
+  uintptr_t bits = 0;
+  for (int q = 0; q < 4; ++q) bits |= (uintptr_t)a.in.avg[q] | (uintptr_t)a.in.lo[q];
+  for (int f = 0; f < 3; ++f)
+    for (int k = 0; k < 4; ++k) bits |= (uintptr_t)a.in.pt[f][k];
+  return (bits & 15) == 0;
+}
+
+// Encodes the tensor maps of the 20 input planes in `a` (row-major nx x ny
+// floats, staging box of the fused tile geometry); false if the driver lacks the
+// encoder or rejects a map.
+inline bool encode_tile_maps(const StepArgs<float>& a, TileMaps* out) {
+  typedef CUresult (*Encode)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                             const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                             const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                             CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    enc = (Encode)fn;
+  }
   using G = FusedGeom<FUSED_TX, FUSED_TY>;
+  const cuuint64_t dims[2] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)a.nx * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)G::SW, (cuuint32_t)G::CH}, unit[2] = {1, 1};
+  for (int p = 0; p < 20; ++p) {
+    float* base = p < 12 ? a.in.pt[p >> 2][p & 3] : p < 16 ? a.in.avg[p - 12] : a.in.lo[p - 16];
+    if (enc(&out->m[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, unit,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
+// One step of the grid described by `a`: the persistent pipelined kernel on
+// `ctas` CTAs when `pipe` is set and the grid allows it (tensor-copy staging
+// when `maps` is given), else one CTA per tile.
+template <bool COMP>
+inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a, bool pipe,
+                                     int ctas, const TileMaps* maps) {
+  using G = FusedGeom<FUSED_TX, FUSED_TY>;
+  const int tcols = (a.nx + FUSED_TX - 1) / FUSED_TX, trows = (a.ny + FUSED_TY - 1) / FUSED_TY;
+  if (pipe && ctas > 0 && pipe_eligible(a)) {
+    auto kern = k_fused_step_pipe<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)G::SMEM_PIPE);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    static TileMaps none;
+    const int ntiles = tcols * trows;
+    kern<<<ntiles < ctas ? ntiles : ctas, FUSED_NT, G::SMEM_PIPE, s>>>(a, maps ? *maps : none,
+                                                                         maps ? 1 : 0);
+    return cudaGetLastError();
+  }
   auto kern = k_fused_step<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
   static bool configured = false;
   if (!configured) {
@@ -525,7 +786,7 @@ inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grd((a.nx + FUSED_TX - 1) / FUSED_TX, (a.ny + FUSED_TY - 1) / FUSED_TY);
+  dim3 grd(tcols, trows);
   kern<<<grd, FUSED_NT, G::SMEM, s>>>(a);
   return cudaGetLastError();
 }

@@ -42,8 +42,9 @@ def test_library_exports_every_declared_entry_point(libaf):
 
 def test_status_strings(libaf):
     libaf.af_status_string.restype = ctypes.c_char_p
-    for s in range(8):
-        assert libaf.af_status_string(s)
+    for s in range(9):
+        assert libaf.af_status_string(s) != b"unknown status"
+    assert libaf.af_status_string(9) == b"unknown status"
 
 
 def test_init_rejects_bad_arguments_without_touching_the_gpu(libaf):

@@ -169,17 +169,21 @@ def test_device_tensors_and_stream():
     s.close()
 
 
-def _with_path(path, fn):
+def _with_env(name, value, fn):
     import os
-    old = os.environ.get("AF_PATH")
-    os.environ["AF_PATH"] = path
+    old = os.environ.get(name)
+    os.environ[name] = value
     try:
         return fn()
     finally:
         if old is None:
-            del os.environ["AF_PATH"]
+            del os.environ[name]
         else:
-            os.environ["AF_PATH"] = old
+            os.environ[name] = old
+
+
+def _with_path(path, fn):
+    return _with_env("AF_PATH", path, fn)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
@@ -193,11 +197,46 @@ def test_fused_matches_unfused_path(precision, shape):
     assert rel_linf(a, b) < 5e-6
 
 
+@pytest.mark.parametrize("tma", ["1", "0"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
+@pytest.mark.parametrize("shape,ctas", [((40, 38), "1"), ((72, 44), "2"), ((100, 70), "3"),
+                                        ((128, 160), "7"), ((424, 392), "")])
+def test_pipelined_kernel_is_bitwise_the_per_tile_kernel(precision, shape, ctas, tma):
+    """The persistent kernel (tiles stepped through by few CTAs, the next tile's
+    input copied while the current one finishes) computes exactly what one CTA per
+    tile computes, whether interior tiles are staged by tensor copies or, like the
+    tiles on the periodic boundary, by cp.async (AF_TMA=0); (40, 38) is the
+    smallest grid it accepts, and 424 x 392 (182 tiles, ragged in both directions)
+    runs on the default one-wave grid."""
+    nx, ny = shape
+    P = I.random_smooth(nx, ny, seed=5 + nx, amp=0.06)
+
+    def pipelined():
+        if ctas:
+            return _with_env("AF_PIPE", ctas, lambda: run_gpu(P, 10, precision))
+        import os
+        assert "AF_PIPE" not in os.environ
+        return run_gpu(P, 10, precision)
+    a = _with_env("AF_TMA", tma, pipelined)
+    b = _with_env("AF_PIPE", "0", lambda: run_gpu(P, 10, precision))
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("variant", ["tai", "rb"])
 def test_fused_fp32_matches_oracle_random(orc, variant):
     P = I.random_smooth(70, 45, seed=4, amp=0.06)
     dt = P.dt * (0.6 if variant == "rb" else 1.0)
     got = _with_path("fused", lambda: run_gpu(P, 20, "fp32_comp", variant, dt))
+    want = run_orc(orc, P, 20, 0 if variant == "tai" else 1, dt)
+    assert rel_linf(got, want) < TOL32
+
+
+@pytest.mark.parametrize("variant", ["tai", "rb"])
+def test_pipelined_fp32_matches_oracle_random(orc, variant):
+    """Persistent kernel with two CTAs over a 3 x 2 tile grid against the oracle."""
+    P = I.random_smooth(76, 48, seed=9, amp=0.06)
+    dt = P.dt * (0.6 if variant == "rb" else 1.0)
+    got = _with_env("AF_PIPE", "2", lambda: run_gpu(P, 20, "fp32_comp", variant, dt))
     want = run_orc(orc, P, 20, 0 if variant == "tai" else 1, dt)
     assert rel_linf(got, want) < TOL32
 
