@@ -10,8 +10,11 @@ value      device-timed cell-updates/s of K steps (CUDA events on the solver's
 e2e        the same metric through the public API with host buffers: every step
            copies the state in from pinned host memory, advances it and copies
            it back out.
-roofline   the dominant kernel (the fused step kernel): algorithmic bytes per
-           launch / its mean CUDA-event duration, against the measured HBM peak.
+roofline   the dominant kernel (the fused step kernel), timed per launch with CUDA
+           events: its algorithmic FP32 lane operations per launch / duration
+           against 152 SMs x 128 FP32 lanes x SM clock ("alu", the bound), and
+           inside it ("hbm") the algorithmic bytes per launch / duration against
+           the measured HBM peak.
 cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
 --impl reference  times the oracle itself (this workload has no other
            reference implementation), on rank 0 only.
@@ -72,7 +75,15 @@ FUSED_SOURCES = ["paper_2605_12915_gb300/csrc/af_fused.cuh",
                  "paper_2605_12915_gb300/csrc/af_common.cuh",
                  "paper_2605_12915_gb300/csrc/af_stencils.cuh",
                  "paper_2605_12915_gb300/csrc/af_ref_kernels.cuh"]
-PROFILE = "profiles/k_fused_step_shear2048_fp32comp.md"
+PROFILE = "profiles/k_fused_step_pipe_shear2048_fp32comp.md"
+
+
+def fused_kernel_name(nx, ny):
+    """The FP32 step kernel the library launches for an nx x ny grid: the
+    persistent pipelined kernel when the grid allows it and AF_PIPE is not 0."""
+    if os.environ.get("AF_PIPE") == "0" or nx % 4 or nx < 40 or ny < 38:
+        return "k_fused_step"
+    return "k_fused_step_pipe"
 
 
 def fused_source_hash():
@@ -297,12 +308,17 @@ def main():
     sm_hz = 1e6 * (csum["sm_max_mhz"] or 2070.0)
     alu_peak = 152 * 128 * sm_hz / 1e12
     alu_ach = ALU_OPS_PER_CELL * N / (kstats["ms_per_launch"] * 1e-3) / 1e12
-    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": profiled_traffic(N) if fused else None, "kernel": kstats["kernel"],
-            "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell,
-            "alu": {"achieved": alu_ach, "peak": alu_peak, "unit": "T FP32 op/s",
-                    "frac": alu_ach / alu_peak, "ops_per_cell": ALU_OPS_PER_CELL,
-                    "note": "the path is issue/ALU bound; peak = 152 SMs x 128 FP32 lanes x SM clock"}}
+    hbm_part = {"achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell}
+    if fused:
+        # FP32 stencil arithmetic on the CUDA cores binds the fused kernel (DRAM
+        # runs near a tenth of its peak)
+        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "T FP32 op/s",
+                "frac": alu_ach / alu_peak, "ops_per_cell": ALU_OPS_PER_CELL,
+                "peak_kind": "152 SMs x 128 FP32 lanes x max SM clock",
+                "traffic": profiled_traffic(N), "kernel": kstats["kernel"], "hbm": hbm_part}
+    else:
+        roof = dict(bound="hbm", traffic=None, kernel=kstats["kernel"], **hbm_part)
     fp64 = fp64_compare(af, I, P, solver_state_after(af, P, args, stream), args, stream, torch) \
         if args.fp64_steps > 0 else None
     adjoint = adjoint_cost(af, P, args, stream, torch, kstats["ms_per_launch"]) \
@@ -458,8 +474,8 @@ def solver_kernel_stats(af, solver, P, stream, torch, reps, fused):
     ev[-1].synchronize()
     ts = [ev[r].elapsed_time(ev[r + 1]) for r in range(reps)]
     if fused:
-        return {"ms_per_launch": float(np.mean(ts)), "kernel": "k_fused_step",
-                "launches_per_step": 1}
+        return {"ms_per_launch": float(np.mean(ts)),
+                "kernel": fused_kernel_name(P.grid.nx, P.grid.ny), "launches_per_step": 1}
     return {"ms_per_launch": float(np.mean(ts)), "kernel": "all 10 launches of one step",
             "launches_per_step": 10}
 

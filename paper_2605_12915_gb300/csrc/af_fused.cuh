@@ -140,6 +140,106 @@ __device__ __forceinline__ int foot_axis(int o, float d, float l[3]) {
   return (int)fl;
 }
 
+// Work item t of a W x H block of cells, visited as 32-wide row chunks first
+// (a warp then reads consecutive addresses of one row: no bank conflicts from
+// row ends inside a warp) and the remaining W % 32 columns after them.
+template <int W, int H>
+__device__ __forceinline__ void chunked_xy(int t, int& x, int& y) {
+  constexpr int MW = W / 32 * 32, RW = W - MW;
+  if constexpr (RW == 0) {
+    x = t % MW;
+    y = t / MW;
+  } else if constexpr (MW == 0) {
+    x = t % W;
+    y = t / W;
+  } else {
+    if (t < MW * H) {
+      x = t % MW;
+      y = t / MW;
+    } else {
+      const int u = t - MW * H;
+      x = MW + u % RW;
+      y = u / RW;
+    }
+  }
+}
+
+// Segments of the acoustic work list: the row chunks (M = W / 32 * 32 columns)
+// or the remaining W - M columns of family f's W x H block.
+template <int M, int H>
+__device__ __forceinline__ bool seg_main(int& u, int f, int& fam, int& dx, int& dy) {
+  if constexpr (M > 0) {
+    if (u < M * H) {
+      fam = f; dx = u % M; dy = u / M;
+      return true;
+    }
+    u -= M * H;
+  }
+  return false;
+}
+template <int M, int W, int H>
+__device__ __forceinline__ bool seg_rest(int& u, int f, int& fam, int& dx, int& dy) {
+  constexpr int R = W - M;
+  if constexpr (R > 0) {
+    if (u < R * H) {
+      fam = f; dx = M + u % R; dy = u / R;
+      return true;
+    }
+    u -= R * H;
+  }
+  return false;
+}
+
+// Acoustic work item t -> (family, D cell): the row chunks of the four
+// families (V (TX+4)x(TY+4), E_v (TX+4)x(TY+3), E_h (TX+3)x(TY+4), C
+// (TX+3)x(TY+3)) first, each starting at a multiple of 32, then their
+// remaining columns.
+template <int TX, int TY>
+__device__ __forceinline__ void acoustic_item(int t, int& fam, int& dx, int& dy) {
+  constexpr int W0 = TX + 4, W1 = TX + 4, W2 = TX + 3, W3 = TX + 3;
+  constexpr int H0 = TY + 4, H1 = TY + 3, H2 = TY + 4, H3 = TY + 3;
+  constexpr int M0 = W0 / 32 * 32, M1 = W1 / 32 * 32, M2 = W2 / 32 * 32, M3 = W3 / 32 * 32;
+  int u = t;
+  fam = 3; dx = 0; dy = 0;
+  if (seg_main<M0, H0>(u, 0, fam, dx, dy) || seg_main<M1, H1>(u, 1, fam, dx, dy) ||
+      seg_main<M2, H2>(u, 2, fam, dx, dy) || seg_main<M3, H3>(u, 3, fam, dx, dy) ||
+      seg_rest<M0, W0, H0>(u, 0, fam, dx, dy) || seg_rest<M1, W1, H1>(u, 1, fam, dx, dy) ||
+      seg_rest<M2, W2, H2>(u, 2, fam, dx, dy))
+    return;
+  seg_rest<M3, W3, H3>(u, 3, fam, dx, dy);
+}
+
+// Point work item t -> (family, point cell) of three PW x PH families: the row
+// chunks of the three families first, then their remaining columns.
+template <int PW, int PH>
+__device__ __forceinline__ void point_item(int t, int& fam, int& px, int& py) {
+  constexpr int MP = PW / 32 * 32, RP = PW - MP;
+  if constexpr (MP == 0) {
+    fam = t / (PW * PH);
+    const int u = t - fam * (PW * PH);
+    px = u % PW;
+    py = u / PW;
+  } else if constexpr (RP == 0) {
+    fam = t / (MP * PH);
+    const int u = t - fam * (MP * PH);
+    px = u % MP;
+    py = u / MP;
+  } else {
+    if (t < 3 * MP * PH) {
+      fam = t / (MP * PH);
+      const int u = t - fam * (MP * PH);
+      px = u % MP;
+      py = u / MP;
+    } else {
+      const int u = t - 3 * MP * PH;
+      fam = u / (RP * PH);
+      const int v = u - fam * (RP * PH);
+      px = MP + v % RP;
+      py = v / RP;
+    }
+  }
+}
+
 // index in [-n, 2n) wrapped into [0, n)
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -202,15 +302,20 @@ __device__ __forceinline__ void issue_tile_async(const StepArgs<float>& a, const
   constexpr int QW = G::SW / 4, CH = G::CH, NPL = COMP ? 20 : 16;
   const unsigned sbase = smem_addr(S);
   if (pc.tm && box_inside<TX, TY>(a.nx, a.ny, i0, j0)) {
-    if (threadIdx.x == 0) {
+    // lane 0 of each warp issues the copies of planes w, w + NT/32, ...; thread 0
+    // also arrives with the byte count (a copy may complete before that: the
+    // phase cannot end before the single arrival)
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0 && w < NPL) {
       // the region was last read by generic loads of every thread (ordered by
       // the barrier before this call)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(pc.bar),
-                   "r"((unsigned)(NPL * CH * G::SW * sizeof(float)))
-                   : "memory");
+      if (w == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(pc.bar),
+                     "r"((unsigned)(NPL * CH * G::SW * sizeof(float)))
+                     : "memory");
 #pragma unroll 1
-      for (int p = 0; p < NPL; ++p)
+      for (int p = w; p < NPL; p += NT / 32)
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3}], [%4];" ::"r"(sbase + 4u * (unsigned)(p * G::SPL)),
@@ -253,16 +358,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
   unsigned bad = 0;
 
   // ---- L2 prefetch of a later tile --------------------------------------------
-  if (PIPE && pc.tm) {
-    if (pf && pi0 >= 0 && threadIdx.x == 0 && box_inside<TX, TY>(nx, ny, pi0, pj0)) {
-#pragma unroll 1
-      for (int p = 0; p < (COMP ? 20 : 16); ++p)
-        asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                         &pc.tm->m[p]),
-                     "r"(pi0 - 4), "r"(pj0 - 2)
-                     : "memory");
-    }
-  } else {
+  {
     if (pf && pi0 >= 0 && (nx & 3) == 0) {
       if (pi0 >= 4 && pj0 >= 2 && pi0 + TX + 4 <= nx && pj0 + CH - 2 <= ny) {
         constexpr int NPF = 20 * CH;  // one 16-byte-aligned row segment per plane and row
@@ -300,11 +396,13 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     for (int t = threadIdx.x; t < CW * CH; t += NT) {
-      const int cx = t % CW, cy = t / CW;
+      int cx, cy;
+      chunked_xy<CW, CH>(t, cx, cy);
       const float* S = D + cy * G::SW + cx + 2;
+      const int w = cy * CW + cx;
 #pragma unroll
       for (int f = 0; f < 3; ++f)
-        W[f * WPL + t] = make_float4(S[(4 * f) * G::SPL], S[(4 * f + 1) * G::SPL],
+        W[f * WPL + w] = make_float4(S[(4 * f) * G::SPL], S[(4 * f + 1) * G::SPL],
                                      S[(4 * f + 2) * G::SPL], S[(4 * f + 3) * G::SPL]);
     }
   } else {
@@ -368,7 +466,8 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
   constexpr int APL = PIPE ? G::SPL : WPL, ARS = PIPE ? G::SW : CW, AOF = PIPE ? 2 : 0;
   constexpr int AB = PIPE ? 12 * G::SPL : 0;
   for (int t = threadIdx.x; t < (CW - 1) * (CH - 1); t += NT) {
-    const int cx = t % (CW - 1), cy = t / (CW - 1);
+    int cx, cy;
+    chunked_xy<CW - 1, CH - 1>(t, cx, cy);
     const int c = cy * CW + cx, ca = AB + cy * ARS + cx + AOF;
     float ub[4], lo[4], sc[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f}, uc[4];
 #pragma unroll
@@ -405,15 +504,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     const float dth = a.dt / a.h;
     for (int t = threadIdx.x; t < nV + nEv + nEh + nC; t += NT) {
       int fam, dx, dy;
-      if (t < nV) {
-        fam = 0; dx = t % (TX + 4); dy = t / (TX + 4);
-      } else if (t < nV + nEv) {
-        fam = 1; dx = (t - nV) % (TX + 4); dy = (t - nV) / (TX + 4);
-      } else if (t < nV + nEv + nEh) {
-        fam = 2; dx = (t - nV - nEv) % (TX + 3); dy = (t - nV - nEv) / (TX + 3);
-      } else {
-        fam = 3; dx = (t - nV - nEv - nEh) % (TX + 3); dy = (t - nV - nEv - nEh) / (TX + 3);
-      }
+      acoustic_item<TX, TY>(t, fam, dx, dy);
       const int wc = (dy + 1) * CW + (dx + 1), dc = dy * DCW + dx;
       const float4 wk = W[fam * WPL + wc];
       const float rk = gas.rho_ref + wk.x, pk = gas.p_ref + wk.w;
@@ -470,8 +561,8 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     for (int k = 0; k < PER; ++k) {
       const int t = threadIdx.x + k * NT;
       if (t >= NPTS) break;
-      const int fam = t / PPL, rem = t - fam * PPL;
-      const int px = rem % PW, py = rem / PW;
+      int fam, px, py;
+      point_item<PW, G::PH>(t, fam, px, py);
       const int ox = fam == 2 ? 1 : 0, oy = fam == 1 ? 1 : 0;
       const int wcP = (py + 2) * CW + (px + 2);  // W cell of the point's cell
       const float4 wp = W[fam * WPL + wcP];
@@ -538,7 +629,9 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     for (int k = 0; k < PER; ++k) {
       const int t = threadIdx.x + k * NT;
       if (t >= NPTS) break;
-      P[t] = res[k];  // t = fam * PPL + rem
+      int fam, px, py;
+      point_item<PW, G::PH>(t, fam, px, py);
+      P[fam * PPL + py * PW + px] = res[k];
     }
   }
   __syncthreads();
@@ -608,6 +701,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     for (int q = 0; q < 4; ++q) flux[k][q] = lam * F[q];
   }
   __syncthreads();  // W and D are dead from here
+  // the next tile's input streams into D while the fluxes and averages are stored
   if constexpr (PIPE) {
     if (pi0 >= 0) issue_tile_async<TX, TY, NT, COMP>(a, pc, pi0, pj0, D);
   }
@@ -665,10 +759,10 @@ __global__ void __launch_bounds__(NT, MINB)
 
 // Persistent pipelined form: CTA b steps through tiles b, b + G, b + 2G, ...
 // (G = gridDim.x, row-major tile order).  The raw input of its next tile is
-// prefetched into L2 at the start of a tile and copied into shared memory
-// (tensor copies when `use_tma` and the box lies inside the grid, else
-// cp.async) while the current tile stores its fluxes and averages.  Requires
-// the conditions of issue_tile_async.
+// copied into shared memory (tensor copies when `use_tma` and the box lies
+// inside the grid, else cp.async after an L2 prefetch at the start of the
+// tile) while the current tile stores its averages.  Requires the conditions
+// of issue_tile_async.
 template <int TX, int TY, int NT, int MINB, bool COMP>
 __global__ void __launch_bounds__(NT, MINB)
     k_fused_step_pipe(const __grid_constant__ StepArgs<float> a,
@@ -685,6 +779,9 @@ __global__ void __launch_bounds__(NT, MINB)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pc.bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (pc.tm && (threadIdx.x & 31) == 0)
+    for (int p = threadIdx.x >> 5; p < 20; p += NT / 32)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tm.m[p]) : "memory");
   __syncthreads();
   const int tcols = (a.nx + TX - 1) / TX, ntiles = tcols * ((a.ny + TY - 1) / TY);
   int tile = blockIdx.x;
@@ -693,8 +790,9 @@ __global__ void __launch_bounds__(NT, MINB)
   for (; tile < ntiles; tile += gridDim.x) {
     const int nxt = tile + gridDim.x;
     const int pi0 = nxt < ntiles ? (nxt % tcols) * TX : -1, pj0 = (nxt / tcols) * TY;
+    // (an L2 prefetch only pays for cp.async staging; tensor copies are fast enough)
     if (!fused_tile<TX, TY, NT, COMP, true>(a, pc, (tile % tcols) * TX, (tile / tcols) * TY, pi0,
-                                            pj0, a.prefetch_wave > 0))
+                                            pj0, a.prefetch_wave > 0 && !pc.tm))
       break;
   }
 }
