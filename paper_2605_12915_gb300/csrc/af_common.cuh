@@ -53,6 +53,10 @@ struct Gas {
   T rho_ref, p_ref;
 };
 
+// The helpers below spell out their fused multiply-adds: the library is built
+// without contraction, so every copy of an expression rounds the same way (a
+// value computed by two thread blocks must agree bitwise for conservation).
+
 // conservative offsets (rho~, rho u, rho v, E~) of a stored primitive
 // (rho~, u, v, p~): E~ = E - p_ref/(gamma-1) = p~/(gamma-1) + rho |u|^2 / 2
 template <typename T>
@@ -61,19 +65,23 @@ __device__ __forceinline__ void cons_from_stored(const Prim<T>& w, const Gas<T>&
   u[0] = w.r;
   u[1] = rho * w.u;
   u[2] = rho * w.v;
-  u[3] = w.p * g.gm1inv + T(0.5) * rho * (w.u * w.u + w.v * w.v);
+  u[3] = fma(w.p, g.gm1inv, (T(0.5) * rho) * fma(w.u, w.u, w.v * w.v));
+}
+
+// primitive from conservative offsets given 1/rho
+template <typename T>
+__device__ __forceinline__ Prim<T> stored_from_cons_inv(const T u[4], const Gas<T>& g, T inv) {
+  Prim<T> w;
+  w.r = u[0];
+  w.u = u[1] * inv;
+  w.v = u[2] * inv;
+  w.p = g.gm1 * fma(T(-0.5), fma(u[1], w.u, u[2] * w.v), u[3]);
+  return w;
 }
 
 template <typename T>
 __device__ __forceinline__ Prim<T> stored_from_cons(const T u[4], const Gas<T>& g) {
-  Prim<T> w;
-  const T rho = g.rho_ref + u[0];
-  const T inv = T(1) / rho;
-  w.r = u[0];
-  w.u = u[1] * inv;
-  w.v = u[2] * inv;
-  w.p = g.gm1 * (u[3] - T(0.5) * (u[1] * w.u + u[2] * w.v));
-  return w;
+  return stored_from_cons_inv(u, g, T(1) / (g.rho_ref + u[0]));
 }
 
 // Euler fluxes F (x) and G (y) of a stored primitive.  The constant p_ref is
@@ -83,9 +91,9 @@ __device__ __forceinline__ void flux_x(const Prim<T>& w, const Gas<T>& g, T f[4]
   const T rho = g.rho_ref + w.r, p = g.p_ref + w.p;
   const T m = rho * w.u;
   f[0] = m;
-  f[1] = m * w.u + w.p;
+  f[1] = fma(m, w.u, w.p);
   f[2] = m * w.v;
-  f[3] = w.u * (p * g.g_gm1 + T(0.5) * rho * (w.u * w.u + w.v * w.v));
+  f[3] = w.u * fma(p, g.g_gm1, (T(0.5) * rho) * fma(w.u, w.u, w.v * w.v));
 }
 
 template <typename T>
@@ -94,8 +102,8 @@ __device__ __forceinline__ void flux_y(const Prim<T>& w, const Gas<T>& g, T f[4]
   const T m = rho * w.v;
   f[0] = m;
   f[1] = m * w.u;
-  f[2] = m * w.v + w.p;
-  f[3] = w.v * (p * g.g_gm1 + T(0.5) * rho * (w.u * w.u + w.v * w.v));
+  f[2] = fma(m, w.v, w.p);
+  f[3] = w.v * fma(p, g.g_gm1, (T(0.5) * rho) * fma(w.u, w.u, w.v * w.v));
 }
 
 // ---- Q2 Lagrange basis on nodes -1, 0, 1 (Sec. 4) ----------------------------

@@ -134,7 +134,7 @@ __device__ __forceinline__ float q2_eval(const float* pV, const float* pEv, cons
 // local coordinates of a point displaced by d (cells) from lattice offset o (0
 // or 1 half cell): cell offset (floor) and Lagrange weights.
 __device__ __forceinline__ int foot_axis(int o, float d, float l[3]) {
-  const float f = 0.5f * o + d;
+  const float f = fmaf(0.5f, (float)o, d);
   const float fl = floorf(f);
   lagrange3(2.f * (f - fl) - 1.f, l);
   return (int)fl;
@@ -489,7 +489,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) uc[k] = (ub[k] + lo[k]) + (0.0625f * sc[k] + 0.25f * se[k]);
-    const Prim<float> w = stored_from_cons(uc, gas);
+    const Prim<float> w = stored_from_cons_inv(uc, gas, __fdividef(1.f, gas.rho_ref + uc[0]));
     if (!(gas.rho_ref + w.r > 0.f && gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
     W[3 * WPL + c] = make_float4(w.r, w.u, w.v, w.p);
   }
@@ -509,8 +509,9 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       const float4 wk = W[fam * WPL + wc];
       const float rk = gas.rho_ref + wk.x, pk = gas.p_ref + wk.w;
       if (!(rk > 0.f && pk > 0.f)) bad |= FLAG_NONPHYSICAL;
-      const float c = sqrtf(gas.gamma * pk / rk);
-      const float Z = rk * c, Zinv = 1.f / Z;
+      // Z^2 = gamma p rho, c = gamma p / Z: one reciprocal square root (2 ulp)
+      const float gp = gas.gamma * pk, z2 = gp * rk;
+      const float Zinv = rsqrtf(z2), Z = z2 * Zinv, c = gp * Zinv;
       const float r1 = c * dth;
       if (r1 > 0.5f) bad |= FLAG_CFL;
       float Gp[3][4], Guv[3][4];
@@ -595,7 +596,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
                               Ds + (2 * 3 + q) * DPL, Ds + (3 * 3 + q) * DPL, dcf, lx, ly);
         const float rf = gas.rho_ref + rft, pf = gas.p_ref + pft;
         if (!(rf > 0.f && pf > 0.f)) bad |= FLAG_NONPHYSICAL;
-        nw.r = rft + e[2] * rf / (gas.gamma * pf);
+        nw.r = rft + __fdividef(e[2] * rf, gas.gamma * pf);
         nw.u = e[0];
         nw.v = e[1];
         nw.p = pft + e[2];
@@ -605,7 +606,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
         const float du = Ds[(fam * 3 + 0) * DPL + dcp] - wp.y;
         const float dv = Ds[(fam * 3 + 1) * DPL + dcp] - wp.z;
         const float dp = Ds[(fam * 3 + 2) * DPL + dcp];
-        nw.r = rft + dp * (gas.rho_ref + wp.x) / (gas.gamma * (gas.p_ref + wp.w));
+        nw.r = rft + __fdividef(dp * (gas.rho_ref + wp.x), gas.gamma * (gas.p_ref + wp.w));
         nw.u = AF_Q2(n, y, lx, ly) + du;
         nw.v = AF_Q2(n, z, lx, ly) + dv;
         nw.p = pft + dp;
@@ -663,8 +664,11 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     const int t = threadIdx.x + k * NT;
     if (t >= NE) break;
     const bool vert = t < NVE;
-    const int u = vert ? t : t - NVE;
-    const int ex = vert ? u % PW : u % TX, ey = vert ? u / PW : u / TX;
+    int ex, ey;  // row chunks of each edge family first
+    if (vert)
+      chunked_xy<PW, TY>(t, ex, ey);
+    else
+      chunked_xy<TX, G::PH>(t - NVE, ex, ey);
     const int fm = vert ? 1 : 2;              // E_v or E_h
     const int wa = (ey + 2) * CW + (ex + 2);  // W cell of V(ex, ey)
     const int wb = vert ? wa + CW : wa + 1;   // the edge's other vertex
@@ -695,7 +699,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       }
       const float wt = s == 1 ? 4.f : 1.f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) F[q] = fmaf(wt, fa[q] + 4.f * fmid[q] + fb[q], F[q]);
+      for (int q = 0; q < 4; ++q) F[q] = fmaf(wt, fmaf(4.f, fmid[q], fa[q] + fb[q]), F[q]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) flux[k][q] = lam * F[q];
@@ -709,8 +713,16 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
   for (int k = 0; k < PERE; ++k) {
     const int t = threadIdx.x + k * NT;
     if (t >= NE) break;
+    int ex, ey, e;  // vertical edge ey PW + ex, horizontal NVE + ey TX + ex
+    if (t < NVE) {
+      chunked_xy<PW, TY>(t, ex, ey);
+      e = ey * PW + ex;
+    } else {
+      chunked_xy<TX, G::PH>(t - NVE, ex, ey);
+      e = NVE + ey * TX + ex;
+    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) FLX[q * NE + t] = flux[k][q];
+    for (int q = 0; q < 4; ++q) FLX[q * NE + e] = flux[k][q];
   }
   __syncthreads();
 #pragma unroll
