@@ -66,11 +66,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP32 arithmetic operations (an FMA counts once) of one cell-update of the
-# fused step, counted from the code: centre recovery ~200, node freezing ~40,
-# acoustic stencils 695 (generated), two Horner evaluations per node ~216,
-# six point updates ~990, space-time Simpson fluxes ~330, compensated update ~144.
-ALU_OPS_PER_CELL = 2600
+# FP32 arithmetic operations of one cell-update of the fused step, counted
+# from the code (add, subtract, multiply, fused multiply-add, reciprocal,
+# reciprocal square root and floor count once each; comparisons, clamps,
+# conversions and index arithmetic do not count; no halo recomputation):
+# centre recovery 184, freezing of the 4 nodes 36, acoustic stencils 695
+# (generated), increment mixing and the two Horner evaluations of 4 nodes 160,
+# six point updates of 144, space-time Simpson fluxes of 2 edges 278,
+# compensated average update 148.
+ALU_OPS_PER_CELL = 2365
 FUSED_SOURCES = ["paper_2605_12915_gb300/csrc/af_fused.cuh",
                  "paper_2605_12915_gb300/csrc/af_common.cuh",
                  "paper_2605_12915_gb300/csrc/af_stencils.cuh",
@@ -193,7 +197,7 @@ def dist_setup(args):
     return rank, world, local
 
 
-def cpu_baseline(P, sample_n=256, sample_steps=6):
+def cpu_baseline(P, sample_n=512, sample_steps=6):
     """The oracle as it stands on a bounded sample of the same workload: the same
     shear layer on a sample_n^2 grid, sample_steps steps, one host core."""
     import oracle
