@@ -5,12 +5,15 @@
 // cell, through
 //   k_adj_flux      average update and space-time Simpson fluxes (gather)
 //   k_adj_points    transported / additive point update, Q2 evaluation at the
-//                   foot, the two Picard stages (scatter with atomics)
+//                   foot, the two Picard stages (all three point families)
 //   k_adj_acoustic  Horner in r, node freezing (c, Z, r) and the transposed
-//                   acoustic stencils (scatter)
-//   k_adj_center    Simpson inversion (scatter)
-// Adjoints are with respect to the stored variables; the storage offsets of
-// the FP32 modes are constant shifts and do not change them.
+//                   acoustic stencils (all four node families)
+//   k_adj_center    Simpson inversion
+// The scattering kernels add each contribution to global memory with one
+// vector reduction: the adjoints of the lattice nodes and of the increments
+// are kept as 4-wide records per node (FP32: one float4 atomic).  Adjoints are
+// with respect to the stored variables; the storage offsets of the FP32 modes
+// are constant shifts and do not change them.
 #pragma once
 
 #include "af_common.cuh"
@@ -18,48 +21,101 @@
 
 namespace af {
 
-__device__ __forceinline__ void atomic_add(float* p, float v) {
-  if (v != 0.f) atomicAdd(p, v);
-}
-__device__ __forceinline__ void atomic_add(double* p, double v) {
-  if (v != 0.0) atomicAdd(p, v);
-}
-
+// Planes of one adjoint step, all with one stride (elements) from three bases.
 template <typename T>
-struct AdjArgs {
-  StepArgs<T> f;       // forward arguments: in = state^n, intermediates recomputed
-  T* lin[16];          // lambda^{n+1}: averages 0-3, V 4-7, E_v 8-11, E_h 12-15
-  T* lout[16];         // lambda^n (same layout)
-  T* lwc[4];           // adjoint of the recovered centres
-  T* linc[2][4][3];    // adjoint of the increments [tau][family][du, dv, dp]
-  T* lhalf[3][4];      // adjoint of the half-step point values
-  T* lfull[3][4];      // adjoint of the full-step point values
+struct AdjView {
+  const T* st;   // state^n: averages 0-3, points 4 + 4 fam + k
+  const T* sto;  // state^{n+1} of the recomputed step: same layout
+  const T* scr;  // intermediates: centres 0-3, increments 4 + 12 s + 3 fam + k,
+                 // half-step points 28 + 4 fam + k
+  T* lam;        // adjoints, in units of ps: lambda^{n+1} 0-15 and lambda^n of
+                 // the averages 16-19 (planes); node records of family fam at
+                 // 20 + 4 fam (4 values per cell: rho, u, v, p; family 3 is the
+                 // centre); increment records of (s, fam) at 36 + 4 (4 s + fam)
+                 // (du, dv, dp, 0); half- and full-step points 68 + 4 fam + k and
+                 // 80 + 4 fam + k (planes)
+  size_t ps;
+  int nx, ny;
+  T h, dt;
+  Gas<T> gas;
+  int variant;
 };
 
-// adjoint of a lattice of (rho, u, v, p): families 0-2 are points, 3 the centres
+constexpr int LAM_IN = 0, LAM_OUT = 16, LAM_NODE = 20, LAM_INC = 36, LAM_HALF = 68, LAM_FULL = 80;
+constexpr int LAM_PLANES = 92;
+constexpr int SCR_INC = 4, SCR_HALF = 28;
+
+// family of lattice offset (a, b) from a cell's vertex: V, E_v, E_h, C
+__host__ __device__ constexpr int fam_of(int a, int b) {
+  return (a & 1) ? ((b & 1) ? 3 : 2) : ((b & 1) ? 1 : 0);
+}
+
+// cell index wrapped into [0, n): one conditional step for |i| < 2n
+__device__ __forceinline__ int wrapc(int i, int n) {
+  const int w = i < 0 ? i + n : (i >= n ? i - n : i);
+  return (unsigned)w < (unsigned)n ? w : wrapi(i, n);
+}
+
 template <typename T>
-struct LatticeAdj {
-  T* f[4][4];
+__device__ __forceinline__ size_t cell_id(const AdjView<T>& v, int cx, int cy) {
+  return (size_t)wrapc(cy, v.ny) * v.nx + wrapc(cx, v.nx);
+}
+
+// time-n value (rho~, u, v, p~) of the node of family fam of cell id
+template <typename T>
+__device__ __forceinline__ Prim<T> node_w(const AdjView<T>& v, int fam, size_t id) {
+  const T* b = fam < 3 ? v.st + (size_t)(4 + 4 * fam) * v.ps : v.scr;
+  Prim<T> w = {b[id], b[v.ps + id], b[2 * v.ps + id], b[3 * v.ps + id]};
+  return w;
+}
+
+// increments (du, dv, dp) of duration s at the node of family fam of cell id
+template <typename T>
+__device__ __forceinline__ void node_d(const AdjView<T>& v, int s, int fam, size_t id, T d[3]) {
+  const T* b = v.scr + (size_t)(SCR_INC + 12 * s + 3 * fam) * v.ps + id;
+  d[0] = b[0];
+  d[1] = b[v.ps];
+  d[2] = b[2 * v.ps];
+}
+
+// Shared-memory accumulator over the footprint of a BX x BY block: cells
+// [i0-1, i0+BX+2) x [j0-1, j0+BY+2), NPL planes; local plane lp < 16 is the
+// adjoint of lattice plane 4 fam + k (global LAM_NODE + lp), lp >= 16 the
+// adjoint of increment 12 s + 3 fam + k (global LAM_INC + lp - 16).
+// adds (a, b, c, d) to the 4-wide record at p (16-byte aligned)
+__device__ __forceinline__ void add4(float* p, float a, float b, float c, float d) {
+  if (a != 0.f || b != 0.f || c != 0.f || d != 0.f)
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+}
+__device__ __forceinline__ void add4(double* p, double a, double b, double c, double d) {
+  if (a != 0.0) atomicAdd(p, a);
+  if (b != 0.0) atomicAdd(p + 1, b);
+  if (c != 0.0) atomicAdd(p + 2, c);
+  if (d != 0.0) atomicAdd(p + 3, d);
+}
+
+// Accumulator of node and increment adjoints (records of the adjoint arena).
+template <typename T>
+struct VecAdj {
+  T* lam;
+  size_t ps;
   int nx, ny;
-  __device__ __forceinline__ void add(int I, int J, T r, T u, T v, T p) const {
-    const int fam = lattice_family(I, J);
-    const size_t id = (size_t)wrapi(J >> 1, ny) * nx + wrapi(I >> 1, nx);
-    atomic_add(f[fam][0] + id, r);
-    atomic_add(f[fam][1] + id, u);
-    atomic_add(f[fam][2] + id, v);
-    atomic_add(f[fam][3] + id, p);
+  __device__ __forceinline__ size_t cell(int cx, int cy) const {
+    return (size_t)wrapc(cy, ny) * nx + wrapc(cx, nx);
+  }
+  // adjoint of the node of family fam of (unwrapped) cell (cx, cy)
+  __device__ __forceinline__ void node(int fam, int cx, int cy, T r, T u, T w, T p) const {
+    add4(lam + (size_t)(LAM_NODE + 4 * fam) * ps + 4 * cell(cx, cy), r, u, w, p);
+  }
+  __device__ __forceinline__ void inc(int s, int fam, int cx, int cy, T du, T dv, T dp) const {
+    add4(lam + (size_t)(LAM_INC + 4 * (4 * s + fam)) * ps + 4 * cell(cx, cy), du, dv, dp, T(0));
   }
 };
 
 template <typename T>
-__device__ __forceinline__ LatticeAdj<T> lattice_adj_of(const AdjArgs<T>& a) {
-  LatticeAdj<T> L;
-  for (int f = 0; f < 3; ++f)
-    for (int k = 0; k < 4; ++k) L.f[f][k] = a.lout[4 + 4 * f + k];
-  for (int k = 0; k < 4; ++k) L.f[3][k] = a.lwc[k];
-  L.nx = a.f.nx;
-  L.ny = a.f.ny;
-  return L;
+__device__ __forceinline__ VecAdj<T> vec_adj(const AdjView<T>& v) {
+  VecAdj<T> a = {v.lam, v.ps, v.nx, v.ny};
+  return a;
 }
 
 // Transposed Euler flux Jacobians: out += J_F(w)^T l  (stored primitives)
@@ -89,56 +145,6 @@ __device__ __forceinline__ void flux_y_adj(const Prim<T>& w, const Gas<T>& g, co
   o[3] += s * (l[2] + g.g_gm1 * w.v * l[3]);
 }
 
-// ---------------------------------------------------------------------------
-// Average update and fluxes (Eq. af-average-update), gathered per cell: the
-// adjoints of the three point families of cell (i,j) at sigma = 0, 1/2, 1.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_adj_flux(AdjArgs<T> a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int nx = a.f.nx, ny = a.f.ny;
-  if (i >= nx || j >= ny) return;
-  const int im = wrapi(i - 1, nx), jm = wrapi(j - 1, ny);
-  const size_t id = (size_t)j * nx + i, idl = (size_t)j * nx + im, idb = (size_t)jm * nx + i,
-               idlb = (size_t)jm * nx + im;
-  T lfx[4], lfxb[4], lgy[4], lgyl[4];
-  for (int k = 0; k < 4; ++k) {
-    const T c = a.lin[k][id], l = a.lin[k][idl], b = a.lin[k][idb], lb = a.lin[k][idlb];
-    lfx[k] = c - l;    // vertical edge x_i of cell (i,j)
-    lfxb[k] = b - lb;  // vertical edge x_i of cell (i,j-1)
-    lgy[k] = c - b;    // horizontal edge y_j of cell (i,j)
-    lgyl[k] = l - lb;  // horizontal edge y_j of cell (i-1,j)
-    a.lout[k][id] = c;
-  }
-  const T cst = a.f.dt / (T(36) * a.f.h);
-  const T wt[3] = {T(1), T(4), T(1)};
-  T* const* lev[3][3] = {{a.f.in.pt[0], a.f.in.pt[1], a.f.in.pt[2]},
-                         {a.f.half[0], a.f.half[1], a.f.half[2]},
-                         {a.f.out.pt[0], a.f.out.pt[1], a.f.out.pt[2]}};
-  T lvx[4], lvy[4];
-  for (int k = 0; k < 4; ++k) {
-    lvx[k] = lfx[k] + lfxb[k];
-    lvy[k] = lgy[k] + lgyl[k];
-  }
-  for (int s = 0; s < 3; ++s) {
-    const T sc = cst * wt[s];
-    T oV[4] = {T(0), T(0), T(0), T(0)}, oEv[4] = {T(0), T(0), T(0), T(0)},
-      oEh[4] = {T(0), T(0), T(0), T(0)};
-    flux_x_adj(load_pt<T>(lev[s][0], id), a.f.gas, lvx, sc, oV);
-    flux_y_adj(load_pt<T>(lev[s][0], id), a.f.gas, lvy, sc, oV);
-    flux_x_adj(load_pt<T>(lev[s][1], id), a.f.gas, lfx, T(4) * sc, oEv);
-    flux_y_adj(load_pt<T>(lev[s][2], id), a.f.gas, lgy, T(4) * sc, oEh);
-    const T* oo[3] = {oV, oEv, oEh};
-    for (int f = 0; f < 3; ++f)
-      for (int k = 0; k < 4; ++k) {
-        if (s == 0) a.lout[4 + 4 * f + k][id] = oo[f][k];
-        else if (s == 1) a.lhalf[f][k][id] = oo[f][k];
-        else a.lfull[f][k][id] = oo[f][k] + a.lin[4 + 4 * f + k][id];
-      }
-  }
-}
-
 // derivative of the Lagrange basis l_-, l_0, l_+ with respect to s
 template <typename T>
 __device__ __forceinline__ void lagrange3_d(T s, T d[3]) {
@@ -148,61 +154,182 @@ __device__ __forceinline__ void lagrange3_d(T s, T d[3]) {
 }
 
 template <typename T>
-struct IncAdj {
-  T* f[4][3];
-  int nx, ny;
-  __device__ __forceinline__ void add(int I, int J, T du, T dv, T dp) const {
-    const int fam = lattice_family(I, J);
-    const size_t id = (size_t)wrapi(J >> 1, ny) * nx + wrapi(I >> 1, nx);
-    atomic_add(f[fam][0] + id, du);
-    atomic_add(f[fam][1] + id, dv);
-    atomic_add(f[fam][2] + id, dp);
+__device__ __forceinline__ void dcons_dprim_T(const Prim<T>& w, const Gas<T>& g, const T l[4],
+                                              T s, T o[4]) {
+  // o += s (dU/dW)^T l, U = (rho~, rho u, rho v, E~) of the stored primitive
+  const T rho = g.rho_ref + w.r;
+  o[0] += s * (l[0] + w.u * l[1] + w.v * l[2] + T(0.5) * (w.u * w.u + w.v * w.v) * l[3]);
+  o[1] += s * (rho * l[1] + rho * w.u * l[3]);
+  o[2] += s * (rho * l[2] + rho * w.v * l[3]);
+  o[3] += s * (g.gm1inv * l[3]);
+}
+
+template <int FAM, typename T, typename Scatter>
+__device__ __forceinline__ void sac_family_adj(const Scatter& S, const T lGp[3][4],
+                                               const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
+  if (FAM == 0) af_sac_V_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+  if (FAM == 1) af_sac_EV_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+  if (FAM == 2) af_sac_EH_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+  if (FAM == 3) af_sac_C_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+}
+
+
+// ---------------------------------------------------------------------------
+// Average update and fluxes (Eq. af-average-update), gathered per cell: the
+// adjoints of the three point families of cell (i,j) at sigma = 0, 1/2, 1.
+// Writes lambda^n of the averages and the sigma = 0 part of lambda^n of the
+// points (the later kernels add to them), and the adjoints of the half- and
+// full-step points.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ Prim<T> level_pt(const T* base, size_t ps, int f, size_t id) {
+  const T* b = base + (size_t)(4 * f) * ps + id;
+  Prim<T> w = {b[0], b[ps], b[2 * ps], b[3 * ps]};
+  return w;
+}
+
+template <typename T>
+__global__ void k_adj_flux(const __grid_constant__ AdjView<T> v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = v.nx, ny = v.ny;
+  if (i >= nx || j >= ny) return;
+  const size_t ps = v.ps;
+  const int im = wrapc(i - 1, nx), jm = wrapc(j - 1, ny);
+  const size_t id = (size_t)j * nx + i, idl = (size_t)j * nx + im, idb = (size_t)jm * nx + i,
+               idlb = (size_t)jm * nx + im;
+  T lfx[4], lfxb[4], lgy[4], lgyl[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T* lk = v.lam + (size_t)(LAM_IN + k) * ps;
+    const T c = lk[id], l = lk[idl], b = lk[idb], lb = lk[idlb];
+    lfx[k] = c - l;    // vertical edge x_i of cell (i,j)
+    lfxb[k] = b - lb;  // vertical edge x_i of cell (i,j-1)
+    lgy[k] = c - b;    // horizontal edge y_j of cell (i,j)
+    lgyl[k] = l - lb;  // horizontal edge y_j of cell (i-1,j)
+    v.lam[(size_t)(LAM_OUT + k) * ps + id] = c;
   }
-};
+  const T cst = v.dt / (T(36) * v.h);
+  T lvx[4], lvy[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    lvx[k] = lfx[k] + lfxb[k];
+    lvy[k] = lgy[k] + lgyl[k];
+  }
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    // point values at sigma = 0 (state^n), 1/2 (recomputed), 1 (state^{n+1})
+    const T* base = s == 0 ? v.st + 4 * ps : s == 1 ? v.scr + (size_t)SCR_HALF * ps : v.sto + 4 * ps;
+    const T sc = cst * (s == 1 ? T(4) : T(1));
+    T oV[4] = {T(0), T(0), T(0), T(0)}, oEv[4] = {T(0), T(0), T(0), T(0)},
+      oEh[4] = {T(0), T(0), T(0), T(0)};
+    const Prim<T> wV = level_pt(base, ps, 0, id);
+    flux_x_adj(wV, v.gas, lvx, sc, oV);
+    flux_y_adj(wV, v.gas, lvy, sc, oV);
+    flux_x_adj(level_pt(base, ps, 1, id), v.gas, lfx, T(4) * sc, oEv);
+    flux_y_adj(level_pt(base, ps, 2, id), v.gas, lgy, T(4) * sc, oEh);
+    const T* oo[3] = {oV, oEv, oEh};
+    if (s == 0) {
+      // lambda^n of the points starts as their node records (the later kernels add)
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        T* rec = v.lam + (size_t)(LAM_NODE + 4 * f) * ps + 4 * id;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rec[k] = oo[f][k];
+      }
+    } else {
+      const int dst = s == 1 ? LAM_HALF : LAM_FULL;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          T val = oo[f][k];
+          if (s == 2) val += v.lam[(size_t)(LAM_IN + 4 + 4 * f + k) * ps + id];
+          v.lam[(size_t)(dst + 4 * f + k) * ps + id] = val;
+        }
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Point update (Sec. 6.1 steps 3-4; Eq. barsukow-additive), reversed.
 // ---------------------------------------------------------------------------
-template <int FAM, typename T>
-__global__ void k_adj_points(AdjArgs<T> a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const StepArgs<T>& f = a.f;
-  if (i >= f.nx || j >= f.ny) return;
-  const LatticeG<T> L = lattice_of(f);
-  const LatticeAdj<T> LA = lattice_adj_of(a);
+// Q2 evaluation of the time-n lattice (points and centres) in foot cell c
+template <typename T>
+__device__ __forceinline__ Prim<T> eval_w_v(const AdjView<T>& v, const FootCell<T>& c) {
+  T lx[3], ly[3];
+  lagrange3(c.xi, lx);
+  lagrange3(c.eta, ly);
+  Prim<T> s = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    Prim<T> row = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const Prim<T> w = node_w(v, fam_of(q, b), cell_id(v, c.ci + (q >> 1), c.cj + (b >> 1)));
+      row.r = fma(lx[q], w.r, row.r);
+      row.u = fma(lx[q], w.u, row.u);
+      row.v = fma(lx[q], w.v, row.v);
+      row.p = fma(lx[q], w.p, row.p);
+    }
+    s.r = fma(ly[b], row.r, s.r);
+    s.u = fma(ly[b], row.u, s.u);
+    s.v = fma(ly[b], row.v, s.v);
+    s.p = fma(ly[b], row.p, s.p);
+  }
+  return s;
+}
+
+// Q2 evaluation of the increments of duration s in foot cell c
+template <typename T>
+__device__ __forceinline__ void eval_d_v(const AdjView<T>& v, int s, const FootCell<T>& c,
+                                         T out[3]) {
+  T lx[3], ly[3];
+  lagrange3(c.xi, lx);
+  lagrange3(c.eta, ly);
+  out[0] = out[1] = out[2] = T(0);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    T row[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      T d[3];
+      node_d(v, s, fam_of(q, b), cell_id(v, c.ci + (q >> 1), c.cj + (b >> 1)), d);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) row[k] = fma(lx[q], d[k], row[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[k] = fma(ly[b], row[k], out[k]);
+  }
+}
+
+// the point of family FAM of cell (i, j), both durations
+template <int FAM, typename T, typename Acc>
+__device__ __forceinline__ void point_adj(const AdjView<T>& v, const Acc& acc, int i, int j) {
+  const size_t ps = v.ps, id = (size_t)j * v.nx + i;
   const int I = 2 * i + (FAM == 2 ? 1 : 0);
   const int J = 2 * j + (FAM == 1 ? 1 : 0);
-  const Prim<T> wp = L.at(I, J);
-  const size_t id = (size_t)j * f.nx + i;
-  const T hinv = T(1) / f.h;
-  const Gas<T>& g = f.gas;
+  const Prim<T> wp = node_w(v, FAM, id);
+  const T hinv = T(1) / v.h;
+  const Gas<T>& g = v.gas;
   T luP = T(0), lvP = T(0), lrP = T(0), lpP = T(0);
+#pragma unroll 1
   for (int s = 0; s < 2; ++s) {
-    const T th = (s == 0 ? T(0.5) * f.dt : f.dt) * hinv;
-    T* const* lsrc = s == 0 ? a.lhalf[FAM] : a.lfull[FAM];
-    const T ly[4] = {lsrc[0][id], lsrc[1][id], lsrc[2][id], lsrc[3][id]};
+    const T th = (s == 0 ? T(0.5) * v.dt : v.dt) * hinv;
+    const T* lsrc = v.lam + (size_t)((s == 0 ? LAM_HALF : LAM_FULL) + 4 * FAM) * ps + id;
+    const T ly[4] = {lsrc[0], lsrc[ps], lsrc[2 * ps], lsrc[3 * ps]};
     if (ly[0] == T(0) && ly[1] == T(0) && ly[2] == T(0) && ly[3] == T(0)) continue;
-    IncrG<T> D;
-    IncAdj<T> DA;
-    for (int q = 0; q < 4; ++q)
-      for (int k = 0; k < 3; ++k) {
-        D.f[q][k] = f.inc[s][q][k];
-        DA.f[q][k] = a.linc[s][q][k];
-      }
-    D.nx = DA.nx = f.nx;
-    D.ny = DA.ny = f.ny;
     // forward recomputation of the foot (Eq. adv-footpoint)
     const T d1x = -th * wp.u, d1y = -th * wp.v;
     const FootCell<T> c1 = locate<T>(I, J, d1x, d1y);
-    const Prim<T> w1 = eval_w(L, c1);
+    const Prim<T> w1 = eval_w_v(v, c1);
     const T dfx = -th * w1.u, dfy = -th * w1.v;
     const FootCell<T> fc = locate<T>(I, J, dfx, dfy);
-    const Prim<T> wf = eval_w(L, fc);
+    const Prim<T> wf = eval_w_v(v, fc);
     T lwf[4], ld[3];  // adjoints of W_f and of the interpolated increments
-    if (f.variant == 0) {
+    if (v.variant == 0) {
       T d[3];
-      eval_d(D, fc, d);
+      eval_d_v(v, s, fc, d);
       const T rf = g.rho_ref + wf.r, pf = g.p_ref + wf.p;
       const T gp = g.gamma * pf;
       lwf[0] = ly[0] * (T(1) + d[2] / gp);
@@ -214,7 +341,7 @@ __global__ void k_adj_points(AdjArgs<T> a) {
       ld[2] = ly[3] + ly[0] * rf / gp;
     } else {
       T d[3];
-      D.at(I, J, d);
+      node_d(v, s, FAM, id, d);
       const T rp = g.rho_ref + wp.r, pp = g.p_ref + wp.p;
       const T gp = g.gamma * pp;
       lwf[0] = ly[0];
@@ -222,7 +349,7 @@ __global__ void k_adj_points(AdjArgs<T> a) {
       lwf[2] = ly[2];
       lwf[3] = ly[3];
       // nw.r = wf.r + dp rho_P / (gamma p_P), with the increments at P itself
-      DA.add(I, J, ly[1], ly[2], ly[3] + ly[0] * rp / gp);
+      acc.inc(s, FAM, i, j, ly[1], ly[2], ly[3] + ly[0] * rp / gp);
       lrP += ly[0] * d[2] / gp;
       lpP += -ly[0] * d[2] * rp / (gp * pp);
       ld[0] = ld[1] = ld[2] = T(0);
@@ -235,17 +362,20 @@ __global__ void k_adj_points(AdjArgs<T> a) {
     lagrange3_d(fc.xi, dx3);
     lagrange3_d(fc.eta, dy3);
     T lxi = T(0), leta = T(0);
+#pragma unroll
     for (int b = 0; b < 3; ++b)
+#pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const int In = 2 * fc.ci + q, Jn = 2 * fc.cj + b;
+        const int fam = fam_of(q, b), cx = fc.ci + (q >> 1), cy = fc.cj + (b >> 1);
+        const size_t gid = cell_id(v, cx, cy);
         const T wgt = lx[q] * lyb[b];
-        LA.add(In, Jn, wgt * lwf[0], wgt * lwf[1], wgt * lwf[2], wgt * lwf[3]);
-        const Prim<T> wn = L.at(In, Jn);
+        acc.node(fam, cx, cy, wgt * lwf[0], wgt * lwf[1], wgt * lwf[2], wgt * lwf[3]);
+        const Prim<T> wn = node_w(v, fam, gid);
         T dot = wn.r * lwf[0] + wn.u * lwf[1] + wn.v * lwf[2] + wn.p * lwf[3];
-        if (f.variant == 0) {
-          DA.add(In, Jn, wgt * ld[0], wgt * ld[1], wgt * ld[2]);
+        if (v.variant == 0) {
+          acc.inc(s, fam, cx, cy, wgt * ld[0], wgt * ld[1], wgt * ld[2]);
           T dn[3];
-          D.at(In, Jn, dn);
+          node_d(v, s, fam, gid, dn);
           dot += dn[0] * ld[0] + dn[1] * ld[1] + dn[2] * ld[2];
         }
         lxi += dx3[q] * lyb[b] * dot;
@@ -261,12 +391,14 @@ __global__ void k_adj_points(AdjArgs<T> a) {
     lagrange3_d(c1.eta, dy3);
     lxi = T(0);
     leta = T(0);
+#pragma unroll
     for (int b = 0; b < 3; ++b)
+#pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const int In = 2 * c1.ci + q, Jn = 2 * c1.cj + b;
+        const int fam = fam_of(q, b), cx = c1.ci + (q >> 1), cy = c1.cj + (b >> 1);
         const T wgt = lx[q] * lyb[b];
-        LA.add(In, Jn, T(0), wgt * lu1, wgt * lv1, T(0));
-        const Prim<T> wn = L.at(In, Jn);
+        acc.node(fam, cx, cy, T(0), wgt * lu1, wgt * lv1, T(0));
+        const Prim<T> wn = node_w(v, fam, cell_id(v, cx, cy));
         const T dot = wn.u * lu1 + wn.v * lv1;
         lxi += dx3[q] * lyb[b] * dot;
         leta += lx[q] * dy3[b] * dot;
@@ -275,75 +407,89 @@ __global__ void k_adj_points(AdjArgs<T> a) {
     luP += -th * ld1x;
     lvP += -th * ld1y;
   }
-  LA.add(I, J, lrP, luP, lvP, lpP);
+  acc.node(FAM, i, j, lrP, luP, lvP, lpP);
+}
+
+template <int FAM, typename T>
+__global__ void k_adj_points(const __grid_constant__ AdjView<T> v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i < v.nx && j < v.ny) point_adj<FAM>(v, vec_adj(v), i, j);
 }
 
 // ---------------------------------------------------------------------------
 // Acoustic increments (Sec. 6.1 step 1), reversed: Horner in r_s = c tau_s / h,
 // freezing c = sqrt(gamma p / rho), Z = rho c, and the transposed stencils.
 // ---------------------------------------------------------------------------
-template <typename T>
-struct ScatterLattice {
-  const LatticeAdj<T>* LA;
-  int I, J;
-  __device__ __forceinline__ void operator()(int dx, int dy, T lp, T lu, T lv) const {
-    LA->add(I + dx, J + dy, T(0), lu, lv, lp);
+// node values (.p, .u, .v) at lattice offset (dx, dy) from the node of family
+// FAM of cell (ci, cj)
+template <int FAM, typename T>
+struct LoadAdjPUV {
+  const AdjView<T>* v;
+  int ci, cj;
+  __device__ __forceinline__ PUV<T> operator()(int dx, int dy) const {
+    const int ax = ((FAM == 2 || FAM == 3) ? 1 : 0) + dx, by = ((FAM == 1 || FAM == 3) ? 1 : 0) + dy;
+    const Prim<T> w = node_w(*v, fam_of(ax, by), cell_id(*v, ci + (ax >> 1), cj + (by >> 1)));
+    PUV<T> o = {w.p, w.u, w.v};
+    return o;
   }
 };
 
-template <int FAM, typename T, typename Scatter>
-__device__ __forceinline__ void sac_family_adj(const Scatter& S, const T lGp[3][4],
-                                               const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
-  if (FAM == 0) af_sac_V_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
-  if (FAM == 1) af_sac_EV_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
-  if (FAM == 2) af_sac_EH_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
-  if (FAM == 3) af_sac_C_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
-}
+// adds (lp, lu, lv) to the adjoint of the node at lattice offset (dx, dy)
+template <int FAM, typename T, typename Acc>
+struct ScatterAdj {
+  Acc acc;
+  int ci, cj;
+  __device__ __forceinline__ void operator()(int dx, int dy, T lp, T lu, T lv) const {
+    const int ax = ((FAM == 2 || FAM == 3) ? 1 : 0) + dx, by = ((FAM == 1 || FAM == 3) ? 1 : 0) + dy;
+    acc.node(fam_of(ax, by), ci + (ax >> 1), cj + (by >> 1), T(0), lu, lv, lp);
+  }
+};
 
-template <int FAM, typename T>
-__global__ void k_adj_acoustic(AdjArgs<T> a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const StepArgs<T>& f = a.f;
-  if (i >= f.nx || j >= f.ny) return;
-  const size_t id = (size_t)j * f.nx + i;
+template <int FAM, typename T, typename Acc>
+__device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc, int i, int j) {
+  const size_t ps = v.ps, id = (size_t)j * v.nx + i;
   T ld[2][3];
   bool any = false;
-  for (int s = 0; s < 2; ++s)
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T* rec = v.lam + (size_t)(LAM_INC + 4 * (4 * s + FAM)) * ps + 4 * id;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      ld[s][k] = a.linc[s][FAM][k][id];
+      ld[s][k] = rec[k];
       any = any || ld[s][k] != T(0);
     }
+  }
   if (!any) return;
-  const LatticeG<T> L = lattice_of(f);
-  const LatticeAdj<T> LA = lattice_adj_of(a);
-  const int I = 2 * i + ((FAM == 2 || FAM == 3) ? 1 : 0);
-  const int J = 2 * j + ((FAM == 1 || FAM == 3) ? 1 : 0);
-  const Prim<T> wk = L.at(I, J);
-  const T rk = f.gas.rho_ref + wk.r, pk = f.gas.p_ref + wk.p;
-  const T c = sqrt(f.gas.gamma * pk / rk);
+  const Prim<T> wk = node_w(v, FAM, id);
+  const T rk = v.gas.rho_ref + wk.r, pk = v.gas.p_ref + wk.p;
+  const T c = sqrt(v.gas.gamma * pk / rk);
   const T Z = rk * c, Zinv = T(1) / Z;
-  const T dth = f.dt / f.h;
+  const T dth = v.dt / v.h;
   const T r1 = c * dth;
   T Gp[3][4], Guv[3][4];
-  LoadPUV<T> ldr = {&L, I, J};
+  const LoadAdjPUV<FAM, T> ldr = {&v, i, j};
   sac_family<FAM, T>(ldr, wk.p, wk.u, wk.v, Gp, Guv);
   // polynomial coefficients c_o[q] (q = 1..4 stored at 0..3), as in increments_at
   T co[3][4];
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
-    co[2][q] = fma(Z, Guv[0][q], Gp[0][q]);   // dp
+    co[2][q] = fma(Z, Guv[0][q], Gp[0][q]);     // dp
     co[0][q] = fma(Zinv, Gp[1][q], Guv[1][q]);  // du
     co[1][q] = fma(Zinv, Gp[2][q], Guv[2][q]);  // dv
   }
   T lco[3][4] = {}, lr1 = T(0);
+#pragma unroll
   for (int s = 0; s < 2; ++s) {
     const T rs = s == 0 ? T(0.5) * r1 : r1;
     const T sc = s == 0 ? T(0.5) : T(1);
     T pw[5];
     pw[0] = T(1);
+#pragma unroll
     for (int q = 1; q <= 4; ++q) pw[q] = pw[q - 1] * rs;
+#pragma unroll
     for (int o = 0; o < 3; ++o) {
       T dr = T(0);
+#pragma unroll
       for (int q = 1; q <= 4; ++q) {
         lco[o][q - 1] += pw[q] * ld[s][o];
         dr += T(q) * pw[q - 1] * co[o][q - 1];
@@ -352,6 +498,7 @@ __global__ void k_adj_acoustic(AdjArgs<T> a) {
     }
   }
   T lGp[3][4], lGuv[3][4], lZ = T(0), lZinv = T(0);
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
     lGp[0][q] = lco[2][q];
     lGuv[0][q] = Z * lco[2][q];
@@ -365,57 +512,96 @@ __global__ void k_adj_acoustic(AdjArgs<T> a) {
   }
   lZ -= lZinv * Zinv * Zinv;
   const T lc = dth * lr1 + rk * lZ;
-  T lrho = c * lZ - lc * c / (T(2) * rk);
-  T lp = lc * c / (T(2) * pk);
+  const T lrho = c * lZ - lc * c / (T(2) * rk);
+  const T lp = lc * c / (T(2) * pk);
   T lpK = T(0), luK = T(0), lvK = T(0);
-  ScatterLattice<T> S = {&LA, I, J};
+  const ScatterAdj<FAM, T, Acc> S = {acc, i, j};
   sac_family_adj<FAM, T>(S, lGp, lGuv, lpK, luK, lvK);
-  LA.add(I, J, lrho, luK, lvK, lp + lpK);
+  acc.node(FAM, i, j, lrho, luK, lvK, lp + lpK);
+}
+
+template <int FAM, typename T>
+__global__ void k_adj_acoustic(const __grid_constant__ AdjView<T> v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i < v.nx && j < v.ny) acoustic_adj<FAM>(v, vec_adj(v), i, j);
 }
 
 // ---------------------------------------------------------------------------
 // Centre recovery (Eq. center-node), reversed.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void dcons_dprim_T(const Prim<T>& w, const Gas<T>& g, const T l[4],
-                                              T s, T o[4]) {
-  // o += s (dU/dW)^T l, U = (rho~, rho u, rho v, E~) of the stored primitive
-  const T rho = g.rho_ref + w.r;
-  o[0] += s * (l[0] + w.u * l[1] + w.v * l[2] + T(0.5) * (w.u * w.u + w.v * w.v) * l[3]);
-  o[1] += s * (rho * l[1] + rho * w.u * l[3]);
-  o[2] += s * (rho * l[2] + rho * w.v * l[3]);
-  o[3] += s * (g.gm1inv * l[3]);
+__global__ void k_adj_center(const __grid_constant__ AdjView<T> v) {
+  const VecAdj<T> acc = vec_adj(v);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const size_t ps = v.ps;
+  if (i < v.nx && j < v.ny) {
+    const size_t id = (size_t)j * v.nx + i;
+    const T* lc = v.lam + (size_t)(LAM_NODE + 12) * ps + 4 * id;  // the centre node's record
+    const T lw[4] = {lc[0], lc[1], lc[2], lc[3]};
+    if (lw[0] != T(0) || lw[1] != T(0) || lw[2] != T(0) || lw[3] != T(0)) {
+      const Gas<T>& g = v.gas;
+      // the recovered centre (rho~, u, v, p~) is W(U_c); lambda_U = (dW/dU)^T lambda_W
+      const T rho = g.rho_ref + v.scr[id], u = v.scr[ps + id], w = v.scr[2 * ps + id];
+      const T ri = T(1) / rho;
+      T lU[4];
+      lU[0] = lw[0] - u * ri * lw[1] - w * ri * lw[2] + g.gm1 * T(0.5) * (u * u + w * w) * lw[3];
+      lU[1] = ri * lw[1] - g.gm1 * u * lw[3];
+      lU[2] = ri * lw[2] - g.gm1 * w * lw[3];
+      lU[3] = g.gm1 * lw[3];
+      // U_c = 9/4 Ubar - 1/16 sum_corners U(W) - 1/4 sum_edges U(W); the
+      // average of this cell has no other writer in this kernel
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v.lam[(size_t)(LAM_OUT + k) * ps + id] += T(2.25) * lU[k];
+      constexpr int nodes[8][2] = {{0, 0}, {2, 0}, {0, 2}, {2, 2}, {1, 0}, {1, 2}, {0, 1}, {2, 1}};
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        const int fam = fam_of(nodes[n][0], nodes[n][1]);
+        const int cx = i + (nodes[n][0] >> 1), cy = j + (nodes[n][1] >> 1);
+        const Prim<T> wn = node_w(v, fam, cell_id(v, cx, cy));
+        T o[4] = {T(0), T(0), T(0), T(0)};
+        dcons_dprim_T(wn, g, lU, n < 4 ? T(-0.0625) : T(-0.25), o);
+        acc.node(fam, cx, cy, o[0], o[1], o[2], o[3]);
+      }
+    }
+  }
 }
 
-template <typename T, bool COMP>
-__global__ void k_adj_center(AdjArgs<T> a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const StepArgs<T>& f = a.f;
-  if (i >= f.nx || j >= f.ny) return;
-  const size_t id = (size_t)j * f.nx + i;
-  const T lw[4] = {a.lwc[0][id], a.lwc[1][id], a.lwc[2][id], a.lwc[3][id]};
-  if (lw[0] == T(0) && lw[1] == T(0) && lw[2] == T(0) && lw[3] == T(0)) return;
-  const Gas<T>& g = f.gas;
-  // the recovered centre (rho~, u, v, p~) is W(U_c); lambda_U = (dW/dU)^T lambda_W
-  const T rho = g.rho_ref + f.wc[0][id], u = f.wc[1][id], v = f.wc[2][id];
-  const T ri = T(1) / rho;
-  T lU[4];
-  lU[0] = lw[0] - u * ri * lw[1] - v * ri * lw[2] + g.gm1 * T(0.5) * (u * u + v * v) * lw[3];
-  lU[1] = ri * lw[1] - g.gm1 * u * lw[3];
-  lU[2] = ri * lw[2] - g.gm1 * v * lw[3];
-  lU[3] = g.gm1 * lw[3];
-  // U_c = 9/4 Ubar - 1/16 sum_corners U(W) - 1/4 sum_edges U(W)
-  for (int k = 0; k < 4; ++k) atomic_add(a.lout[k] + id, T(2.25) * lU[k]);
-  const LatticeAdj<T> LA = lattice_adj_of(a);
-  const LatticeG<T> L = lattice_of(f);
-  const int I = 2 * i, J = 2 * j;
-  const int nodes[8][2] = {{0, 0}, {2, 0}, {0, 2}, {2, 2}, {1, 0}, {1, 2}, {0, 1}, {2, 1}};
-  for (int n = 0; n < 8; ++n) {
-    const Prim<T> w = L.at(I + nodes[n][0], J + nodes[n][1]);
-    T o[4] = {T(0), T(0), T(0), T(0)};
-    dcons_dprim_T(w, g, lU, n < 4 ? T(-0.0625) : T(-0.25), o);
-    LA.add(I + nodes[n][0], J + nodes[n][1], o[0], o[1], o[2], o[3]);
+// Sixteen planes converted in one launch (the adjoint state in and out).
+template <typename A, typename B>
+struct Cast16 {
+  const A* src[16];
+  B* dst[16];
+};
+
+template <typename A, typename B>
+__global__ void k_cast16(const __grid_constant__ Cast16<A, B> c, size_t n) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int p = 0; p < 16; ++p) c.dst[p][t] = (B)c.src[p][t];
+  }
+}
+
+// lambda^n out: the averages' planes and the point families' node records into
+// sixteen FP64 planes
+template <typename T>
+struct AdjOut {
+  double* dst[16];
+};
+
+template <typename T>
+__global__ void k_adj_out(const __grid_constant__ AdjView<T> v,
+                          const __grid_constant__ AdjOut<T> o, size_t n) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o.dst[k][t] = (double)v.lam[(size_t)(LAM_OUT + k) * v.ps + t];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const T* rec = v.lam + (size_t)(LAM_NODE + 4 * f) * v.ps + 4 * t;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) o.dst[4 + 4 * f + k][t] = (double)rec[k];
+    }
   }
 }
 

@@ -45,7 +45,7 @@ struct af_handle {
   int pipe_ctas;         // CTAs of the persistent pipelined fused kernel (0: off)
   TileMaps* tmaps;       // tensor maps of the input planes of state[0], state[1]
   int tma;               // 1: the pipelined kernel stages interior tiles by tensor copies
-  void* adj_arena;       // adjoint planes (lazy): lin 16, lout 16, lwc 4, linc 24, lhalf 12, lfull 12
+  void* adj_arena;       // adjoint arena (lazy): LAM_PLANES planes, see AdjView
 };
 
 namespace {
@@ -268,32 +268,30 @@ namespace {
 template <typename T, bool COMP>
 af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const af_state_f64* lout,
                        af_memory where) {
+  // every plane (state, intermediates, adjoints) has the same padded size
   const size_t plane = (h->N * sizeof(T) + 255) & ~(size_t)255;
-  const int NPL = 84;
-  if (!h->adj_arena && cudaMalloc(&h->adj_arena, plane * NPL) != cudaSuccess) {
+  if (!h->adj_arena && cudaMalloc(&h->adj_arena, plane * LAM_PLANES) != cudaSuccess) {
     h->adj_arena = nullptr;
     return AF_ERR_ALLOC;
   }
-  char* base = (char*)h->adj_arena;
-  auto P = [&](int k) { return (T*)(base + plane * (size_t)k); };
-  AdjArgs<T> a;
-  a.f = step_args<T>(h, dt);
-  int k = 0;
-  for (int q = 0; q < 16; ++q) a.lin[q] = P(k++);
-  for (int q = 0; q < 16; ++q) a.lout[q] = P(k++);
-  for (int q = 0; q < 4; ++q) a.lwc[q] = P(k++);
-  const int linc0 = k;
-  for (int s2 = 0; s2 < 2; ++s2)
-    for (int f = 0; f < 4; ++f)
-      for (int q = 0; q < 3; ++q) a.linc[s2][f][q] = P(k++);
-  for (int f = 0; f < 3; ++f)
-    for (int q = 0; q < 4; ++q) a.lhalf[f][q] = P(k++);
-  for (int f = 0; f < 3; ++f)
-    for (int q = 0; q < 4; ++q) a.lfull[f][q] = P(k++);
+  const StepArgs<T> f = step_args<T>(h, dt);
+  AdjView<T> v;
+  v.st = (const T*)h->state[h->cur][0];
+  v.sto = (const T*)h->state[1 - h->cur][0];
+  v.scr = (const T*)h->scratch[0];
+  v.lam = (T*)h->adj_arena;
+  v.ps = plane / sizeof(T);
+  v.nx = h->nx;
+  v.ny = h->ny;
+  v.h = f.h;
+  v.dt = f.dt;
+  v.gas = f.gas;
+  v.variant = f.variant;
   cudaStream_t s = h->stream;
   // lambda^{n+1} in (FP64 -> working precision, no storage offsets)
   af_status st = ensure_staging(h);
   if (st != AF_OK) return st;
+  Cast16<double, T> cin;
   for (int p = 0; p < 16; ++p) {
     const double* src = plane_in(lin, p);
     if (where == AF_HOST) {
@@ -302,40 +300,43 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
         return cuda_fail(h);
       src = h->staging + (size_t)p * h->N;
     }
-    k_cast<<<grid1d(h->N), 256, 0, s>>>(src, a.lin[p], h->N);
+    cin.src[p] = src;
+    cin.dst[p] = v.lam + (size_t)(LAM_IN + p) * v.ps;
   }
+  k_cast16<<<grid1d(h->N), 256, 0, s>>>(cin, h->N);
   // forward intermediates of the step from the handle's current state
   dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
-  k_center<T, COMP><<<grd, blk, 0, s>>>(a.f);
-  k_acoustic<0, T><<<grd, blk, 0, s>>>(a.f);
-  k_acoustic<1, T><<<grd, blk, 0, s>>>(a.f);
-  k_acoustic<2, T><<<grd, blk, 0, s>>>(a.f);
-  k_acoustic<3, T><<<grd, blk, 0, s>>>(a.f);
-  k_points<0, T><<<grd, blk, 0, s>>>(a.f);
-  k_points<1, T><<<grd, blk, 0, s>>>(a.f);
-  k_points<2, T><<<grd, blk, 0, s>>>(a.f);
-  // reverse sweep
-  if (cudaMemsetAsync(a.lwc[0], 0, plane * 4, s) != cudaSuccess ||
-      cudaMemsetAsync(P(linc0), 0, plane * 24, s) != cudaSuccess)
+  k_center<T, COMP><<<grd, blk, 0, s>>>(f);
+  k_acoustic<0, T><<<grd, blk, 0, s>>>(f);
+  k_acoustic<1, T><<<grd, blk, 0, s>>>(f);
+  k_acoustic<2, T><<<grd, blk, 0, s>>>(f);
+  k_acoustic<3, T><<<grd, blk, 0, s>>>(f);
+  k_points<0, T><<<grd, blk, 0, s>>>(f);
+  k_points<1, T><<<grd, blk, 0, s>>>(f);
+  k_points<2, T><<<grd, blk, 0, s>>>(f);
+  // reverse sweep: the centre and increment records start at zero (planes
+  // LAM_NODE + 12 ... LAM_INC + 31 are contiguous)
+  if (cudaMemsetAsync(v.lam + (size_t)(LAM_NODE + 12) * v.ps, 0, plane * 36, s) != cudaSuccess)
     return cuda_fail(h);
-  k_adj_flux<T><<<grd, blk, 0, s>>>(a);
-  k_adj_points<0, T><<<grd, blk, 0, s>>>(a);
-  k_adj_points<1, T><<<grd, blk, 0, s>>>(a);
-  k_adj_points<2, T><<<grd, blk, 0, s>>>(a);
-  k_adj_acoustic<0, T><<<grd, blk, 0, s>>>(a);
-  k_adj_acoustic<1, T><<<grd, blk, 0, s>>>(a);
-  k_adj_acoustic<2, T><<<grd, blk, 0, s>>>(a);
-  k_adj_acoustic<3, T><<<grd, blk, 0, s>>>(a);
-  k_adj_center<T, COMP><<<grd, blk, 0, s>>>(a);
+  k_adj_flux<T><<<grd, blk, 0, s>>>(v);
+  k_adj_points<0, T><<<grd, blk, 0, s>>>(v);
+  k_adj_points<1, T><<<grd, blk, 0, s>>>(v);
+  k_adj_points<2, T><<<grd, blk, 0, s>>>(v);
+  k_adj_acoustic<0, T><<<grd, blk, 0, s>>>(v);
+  k_adj_acoustic<1, T><<<grd, blk, 0, s>>>(v);
+  k_adj_acoustic<2, T><<<grd, blk, 0, s>>>(v);
+  k_adj_acoustic<3, T><<<grd, blk, 0, s>>>(v);
+  k_adj_center<T><<<grd, blk, 0, s>>>(v);
   // lambda^n out
-  for (int p = 0; p < 16; ++p) {
-    double* dst = where == AF_HOST ? h->staging + (size_t)p * h->N : (double*)plane_in(lout, p);
-    k_cast<<<grid1d(h->N), 256, 0, s>>>(a.lout[p], dst, h->N);
-    if (where == AF_HOST &&
-        cudaMemcpyAsync((void*)plane_in(lout, p), dst, sizeof(double) * h->N,
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return cuda_fail(h);
-  }
+  AdjOut<T> out;
+  for (int p = 0; p < 16; ++p)
+    out.dst[p] = where == AF_HOST ? h->staging + (size_t)p * h->N : (double*)plane_in(lout, p);
+  k_adj_out<T><<<grid1d(h->N), 256, 0, s>>>(v, out, h->N);
+  if (where == AF_HOST)
+    for (int p = 0; p < 16; ++p)
+      if (cudaMemcpyAsync((void*)plane_in(lout, p), h->staging + (size_t)p * h->N,
+                          sizeof(double) * h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return cuda_fail(h);
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
   return af_sync(h);
 }
