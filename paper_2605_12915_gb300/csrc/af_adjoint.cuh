@@ -254,53 +254,39 @@ __global__ void k_adj_flux(const __grid_constant__ AdjView<T> v) {
 // ---------------------------------------------------------------------------
 // Point update (Sec. 6.1 steps 3-4; Eq. barsukow-additive), reversed.
 // ---------------------------------------------------------------------------
-// Q2 evaluation of the time-n lattice (points and centres) in foot cell c
+// the nine nodes of foot cell c in [b][q] order (loaded once: the scatter
+// below reuses them between its atomics)
 template <typename T>
-__device__ __forceinline__ Prim<T> eval_w_v(const AdjView<T>& v, const FootCell<T>& c) {
-  T lx[3], ly[3];
-  lagrange3(c.xi, lx);
-  lagrange3(c.eta, ly);
-  Prim<T> s = {T(0), T(0), T(0), T(0)};
+__device__ __forceinline__ void load_nodes(const AdjView<T>& v, const FootCell<T>& c, Prim<T> w[9]) {
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    Prim<T> row = {T(0), T(0), T(0), T(0)};
+  for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const Prim<T> w = node_w(v, fam_of(q, b), cell_id(v, c.ci + (q >> 1), c.cj + (b >> 1)));
-      row.r = fma(lx[q], w.r, row.r);
-      row.u = fma(lx[q], w.u, row.u);
-      row.v = fma(lx[q], w.v, row.v);
-      row.p = fma(lx[q], w.p, row.p);
-    }
-    s.r = fma(ly[b], row.r, s.r);
-    s.u = fma(ly[b], row.u, s.u);
-    s.v = fma(ly[b], row.v, s.v);
-    s.p = fma(ly[b], row.p, s.p);
-  }
-  return s;
+    for (int q = 0; q < 3; ++q)
+      w[3 * b + q] = node_w(v, fam_of(q, b), cell_id(v, c.ci + (q >> 1), c.cj + (b >> 1)));
 }
 
-// Q2 evaluation of the increments of duration s in foot cell c
 template <typename T>
-__device__ __forceinline__ void eval_d_v(const AdjView<T>& v, int s, const FootCell<T>& c,
-                                         T out[3]) {
-  T lx[3], ly[3];
-  lagrange3(c.xi, lx);
-  lagrange3(c.eta, ly);
-  out[0] = out[1] = out[2] = T(0);
+__device__ __forceinline__ void load_incs(const AdjView<T>& v, int s, const FootCell<T>& c,
+                                          T d[9][3]) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      node_d(v, s, fam_of(q, b), cell_id(v, c.ci + (q >> 1), c.cj + (b >> 1)), d[3 * b + q]);
+}
+
+// sum_qb l_q(xi) l_b(eta) f_qb (rows first, as the forward evaluation)
+template <typename T>
+__device__ __forceinline__ T q2_sum(const T* f, int stride, const T lx[3], const T ly[3]) {
+  T out = T(0);
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    T row[3] = {T(0), T(0), T(0)};
+    T row = T(0);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      T d[3];
-      node_d(v, s, fam_of(q, b), cell_id(v, c.ci + (q >> 1), c.cj + (b >> 1)), d);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) row[k] = fma(lx[q], d[k], row[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) out[k] = fma(ly[b], row[k], out[k]);
+    for (int q = 0; q < 3; ++q) row = fma(lx[q], f[(3 * b + q) * stride], row);
+    out = fma(ly[b], row, out);
   }
+  return out;
 }
 
 // the point of family FAM of cell (i, j), both durations
@@ -322,20 +308,42 @@ __device__ __forceinline__ void point_adj(const AdjView<T>& v, const Acc& acc, i
     // forward recomputation of the foot (Eq. adv-footpoint)
     const T d1x = -th * wp.u, d1y = -th * wp.v;
     const FootCell<T> c1 = locate<T>(I, J, d1x, d1y);
-    const Prim<T> w1 = eval_w_v(v, c1);
-    const T dfx = -th * w1.u, dfy = -th * w1.v;
+    T uv1[9][2];  // (u, v) of the first stage's nodes
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const Prim<T> w = node_w(v, fam_of(q, b), cell_id(v, c1.ci + (q >> 1), c1.cj + (b >> 1)));
+        uv1[3 * b + q][0] = w.u;
+        uv1[3 * b + q][1] = w.v;
+      }
+    T lx1[3], ly1[3];
+    lagrange3(c1.xi, lx1);
+    lagrange3(c1.eta, ly1);
+    const T u1 = q2_sum(&uv1[0][0], 2, lx1, ly1), v1 = q2_sum(&uv1[0][1], 2, lx1, ly1);
+    const T dfx = -th * u1, dfy = -th * v1;
     const FootCell<T> fc = locate<T>(I, J, dfx, dfy);
-    const Prim<T> wf = eval_w_v(v, fc);
+    Prim<T> nf[9];
+    load_nodes(v, fc, nf);
+    T lx[3], lyb[3], dx3[3], dy3[3];
+    lagrange3(fc.xi, lx);
+    lagrange3(fc.eta, lyb);
+    lagrange3_d(fc.xi, dx3);
+    lagrange3_d(fc.eta, dy3);
+    Prim<T> wf;
+    wf.r = q2_sum(&nf[0].r, 4, lx, lyb);
+    wf.p = q2_sum(&nf[0].p, 4, lx, lyb);
     T lwf[4], ld[3];  // adjoints of W_f and of the interpolated increments
+    T df[9][3];
     if (v.variant == 0) {
-      T d[3];
-      eval_d_v(v, s, fc, d);
+      load_incs(v, s, fc, df);
+      const T d2 = q2_sum(&df[0][2], 3, lx, lyb);
       const T rf = g.rho_ref + wf.r, pf = g.p_ref + wf.p;
       const T gp = g.gamma * pf;
-      lwf[0] = ly[0] * (T(1) + d[2] / gp);
+      lwf[0] = ly[0] * (T(1) + d2 / gp);
       lwf[1] = ly[1];
       lwf[2] = ly[2];
-      lwf[3] = ly[3] - ly[0] * d[2] * rf / (gp * pf);
+      lwf[3] = ly[3] - ly[0] * d2 * rf / (gp * pf);
       ld[0] = ly[1];
       ld[1] = ly[2];
       ld[2] = ly[3] + ly[0] * rf / gp;
@@ -356,27 +364,18 @@ __device__ __forceinline__ void point_adj(const AdjView<T>& v, const Acc& acc, i
     }
     // scatter through the Q2 evaluation at the foot and collect the adjoint of
     // the foot's local coordinates
-    T lx[3], lyb[3], dx3[3], dy3[3];
-    lagrange3(fc.xi, lx);
-    lagrange3(fc.eta, lyb);
-    lagrange3_d(fc.xi, dx3);
-    lagrange3_d(fc.eta, dy3);
     T lxi = T(0), leta = T(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const int fam = fam_of(q, b), cx = fc.ci + (q >> 1), cy = fc.cj + (b >> 1);
-        const size_t gid = cell_id(v, cx, cy);
+        const int n = 3 * b + q, fam = fam_of(q, b), cx = fc.ci + (q >> 1), cy = fc.cj + (b >> 1);
         const T wgt = lx[q] * lyb[b];
         acc.node(fam, cx, cy, wgt * lwf[0], wgt * lwf[1], wgt * lwf[2], wgt * lwf[3]);
-        const Prim<T> wn = node_w(v, fam, gid);
-        T dot = wn.r * lwf[0] + wn.u * lwf[1] + wn.v * lwf[2] + wn.p * lwf[3];
+        T dot = nf[n].r * lwf[0] + nf[n].u * lwf[1] + nf[n].v * lwf[2] + nf[n].p * lwf[3];
         if (v.variant == 0) {
           acc.inc(s, fam, cx, cy, wgt * ld[0], wgt * ld[1], wgt * ld[2]);
-          T dn[3];
-          node_d(v, s, fam, gid, dn);
-          dot += dn[0] * ld[0] + dn[1] * ld[1] + dn[2] * ld[2];
+          dot += df[n][0] * ld[0] + df[n][1] * ld[1] + df[n][2] * ld[2];
         }
         lxi += dx3[q] * lyb[b] * dot;
         leta += lx[q] * dy3[b] * dot;
@@ -385,8 +384,6 @@ __device__ __forceinline__ void point_adj(const AdjView<T>& v, const Acc& acc, i
     const T ldfx = T(2) * lxi, ldfy = T(2) * leta;
     const T lu1 = -th * ldfx, lv1 = -th * ldfy;
     // first Picard stage: (u1, v1) = R_h(u, v) at P + d1
-    lagrange3(c1.xi, lx);
-    lagrange3(c1.eta, lyb);
     lagrange3_d(c1.xi, dx3);
     lagrange3_d(c1.eta, dy3);
     lxi = T(0);
@@ -395,13 +392,12 @@ __device__ __forceinline__ void point_adj(const AdjView<T>& v, const Acc& acc, i
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const int fam = fam_of(q, b), cx = c1.ci + (q >> 1), cy = c1.cj + (b >> 1);
-        const T wgt = lx[q] * lyb[b];
+        const int n = 3 * b + q, fam = fam_of(q, b), cx = c1.ci + (q >> 1), cy = c1.cj + (b >> 1);
+        const T wgt = lx1[q] * ly1[b];
         acc.node(fam, cx, cy, T(0), wgt * lu1, wgt * lv1, T(0));
-        const Prim<T> wn = node_w(v, fam, cell_id(v, cx, cy));
-        const T dot = wn.u * lu1 + wn.v * lv1;
-        lxi += dx3[q] * lyb[b] * dot;
-        leta += lx[q] * dy3[b] * dot;
+        const T dot = uv1[n][0] * lu1 + uv1[n][1] * lv1;
+        lxi += dx3[q] * ly1[b] * dot;
+        leta += lx1[q] * dy3[b] * dot;
       }
     const T ld1x = T(2) * lxi, ld1y = T(2) * leta;
     luP += -th * ld1x;
@@ -411,7 +407,7 @@ __device__ __forceinline__ void point_adj(const AdjView<T>& v, const Acc& acc, i
 }
 
 template <int FAM, typename T>
-__global__ void k_adj_points(const __grid_constant__ AdjView<T> v) {
+__global__ void __launch_bounds__(256, 2) k_adj_points(const __grid_constant__ AdjView<T> v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i < v.nx && j < v.ny) point_adj<FAM>(v, vec_adj(v), i, j);
 }
