@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 
 #include "../../include/af.h"
 #include "af_common.cuh"
@@ -304,16 +305,29 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
     cin.dst[p] = v.lam + (size_t)(LAM_IN + p) * v.ps;
   }
   k_cast16<<<grid1d(h->N), 256, 0, s>>>(cin, h->N);
-  // forward intermediates of the step from the handle's current state
+  // forward intermediates of the step from the handle's current state: the
+  // pipelined fused kernel stores them where it runs (FP32 modes), else the
+  // unfused kernels
   dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
-  k_center<T, COMP><<<grd, blk, 0, s>>>(f);
-  k_acoustic<0, T><<<grd, blk, 0, s>>>(f);
-  k_acoustic<1, T><<<grd, blk, 0, s>>>(f);
-  k_acoustic<2, T><<<grd, blk, 0, s>>>(f);
-  k_acoustic<3, T><<<grd, blk, 0, s>>>(f);
-  k_points<0, T><<<grd, blk, 0, s>>>(f);
-  k_points<1, T><<<grd, blk, 0, s>>>(f);
-  k_points<2, T><<<grd, blk, 0, s>>>(f);
+  bool fused_inter = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->fused && h->pipe_ctas > 0 && pipe_eligible(f)) {
+      if (launch_fused_step<COMP, true>(s, f, true, h->pipe_ctas,
+                                        h->tma ? &h->tmaps[h->cur] : nullptr) != cudaSuccess)
+        return cuda_fail(h);
+      fused_inter = true;
+    }
+  }
+  if (!fused_inter) {
+    k_center<T, COMP><<<grd, blk, 0, s>>>(f);
+    k_acoustic<0, T><<<grd, blk, 0, s>>>(f);
+    k_acoustic<1, T><<<grd, blk, 0, s>>>(f);
+    k_acoustic<2, T><<<grd, blk, 0, s>>>(f);
+    k_acoustic<3, T><<<grd, blk, 0, s>>>(f);
+    k_points<0, T><<<grd, blk, 0, s>>>(f);
+    k_points<1, T><<<grd, blk, 0, s>>>(f);
+    k_points<2, T><<<grd, blk, 0, s>>>(f);
+  }
   // reverse sweep: the centre and increment records start at zero (planes
   // LAM_NODE + 12 ... LAM_INC + 31 are contiguous)
   if (cudaMemsetAsync(v.lam + (size_t)(LAM_NODE + 12) * v.ps, 0, plane * 36, s) != cudaSuccess)

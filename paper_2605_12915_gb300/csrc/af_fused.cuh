@@ -341,8 +341,11 @@ __device__ __forceinline__ void issue_tile_async(const StepArgs<float>& a, const
 // its rows are prefetched into L2 when `pf` is set, and with PIPE its raw input
 // is copied asynchronously into the D region once this tile no longer needs it.
 // With PIPE this tile's own input is already on its way there
-// (issue_tile_async); false means the wait for it timed out (flagged).
-template <int TX, int TY, int NT, bool COMP, bool PIPE>
+// (issue_tile_async); false means the wait for it timed out (flagged).  With
+// INTER the tile also stores the intermediates of its owned cells that the
+// adjoint linearises about: centres (a.wc), increments (a.inc) and half-step
+// points (a.half).
+template <int TX, int TY, int NT, bool COMP, bool PIPE, bool INTER = false>
 __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc, int i0, int j0,
                                            int pi0, int pj0, bool pf) {
   using G = FusedGeom<TX, TY>;
@@ -492,6 +495,16 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     const Prim<float> w = stored_from_cons_inv(uc, gas, __fdividef(1.f, gas.rho_ref + uc[0]));
     if (!(gas.rho_ref + w.r > 0.f && gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
     W[3 * WPL + c] = make_float4(w.r, w.u, w.v, w.p);
+    if constexpr (INTER) {
+      const int gi = i0 - 2 + cx, gj = j0 - 2 + cy;
+      if (cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2 && gi < nx && gj < ny) {
+        const size_t id = (size_t)gj * nx + gi;
+        a.wc[0][id] = w.r;
+        a.wc[1][id] = w.u;
+        a.wc[2][id] = w.v;
+        a.wc[3][id] = w.p;
+      }
+    }
   }
   __syncthreads();
 
@@ -534,14 +547,22 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       float d[3];
       float* D0 = D + fam * 3 * DPL + dc;
       float* D1 = D + (4 + fam) * 3 * DPL + dc;
+      // owned node (for the stored intermediates)
+      const int gi = i0 - 1 + dx, gj = j0 - 1 + dy;
+      const bool own = INTER && dx >= 1 && dx <= TX && dy >= 1 && dy <= TY && gi < nx && gj < ny;
+      const size_t gid = own ? (size_t)gj * nx + gi : 0;
       increments_at(Gp, Guv, Z, Zinv, 0.5f * r1, d);
       D0[0] = wk.y + d[0];
       D0[DPL] = wk.z + d[1];
       D0[2 * DPL] = d[2];
+      if (own)
+        for (int k = 0; k < 3; ++k) a.inc[0][fam][k][gid] = d[k];
       increments_at(Gp, Guv, Z, Zinv, r1, d);
       D1[0] = wk.y + d[0];
       D1[DPL] = wk.z + d[1];
       D1[2 * DPL] = d[2];
+      if (own)
+        for (int k = 0; k < 3; ++k) a.inc[1][fam][k][gid] = d[k];
     }
   }
   __syncthreads();
@@ -616,6 +637,13 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       res[k] = make_float4(nw.r, nw.u, nw.v, nw.p);
       // owned points at t^{n+1} go straight to HBM
       const int gi = i0 + px, gj = j0 + py;
+      if (INTER && s == 0 && px < TX && py < TY && gi < nx && gj < ny) {
+        const size_t id = (size_t)gj * nx + gi;
+        a.half[fam][0][id] = nw.r;
+        a.half[fam][1][id] = nw.u;
+        a.half[fam][2][id] = nw.v;
+        a.half[fam][3][id] = nw.p;
+      }
       if (s == 1 && px < TX && py < TY && gi < nx && gj < ny) {
         const size_t id = (size_t)gj * nx + gi;
         a.out.pt[fam][0][id] = nw.r;
@@ -775,7 +803,7 @@ __global__ void __launch_bounds__(NT, MINB)
 // inside the grid, else cp.async after an L2 prefetch at the start of the
 // tile) while the current tile stores its averages.  Requires the conditions
 // of issue_tile_async.
-template <int TX, int TY, int NT, int MINB, bool COMP>
+template <int TX, int TY, int NT, int MINB, bool COMP, bool INTER>
 __global__ void __launch_bounds__(NT, MINB)
     k_fused_step_pipe(const __grid_constant__ StepArgs<float> a,
                       const __grid_constant__ TileMaps tm, int use_tma) {
@@ -803,8 +831,9 @@ __global__ void __launch_bounds__(NT, MINB)
     const int nxt = tile + gridDim.x;
     const int pi0 = nxt < ntiles ? (nxt % tcols) * TX : -1, pj0 = (nxt / tcols) * TY;
     // (an L2 prefetch only pays for cp.async staging; tensor copies are fast enough)
-    if (!fused_tile<TX, TY, NT, COMP, true>(a, pc, (tile % tcols) * TX, (tile / tcols) * TY, pi0,
-                                            pj0, a.prefetch_wave > 0 && !pc.tm))
+    if (!fused_tile<TX, TY, NT, COMP, true, INTER>(a, pc, (tile % tcols) * TX,
+                                                   (tile / tcols) * TY, pi0, pj0,
+                                                   a.prefetch_wave > 0 && !pc.tm))
       break;
   }
 }
@@ -867,14 +896,15 @@ inline bool encode_tile_maps(const StepArgs<float>& a, TileMaps* out) {
 
 // One step of the grid described by `a`: the persistent pipelined kernel on
 // `ctas` CTAs when `pipe` is set and the grid allows it (tensor-copy staging
-// when `maps` is given), else one CTA per tile.
-template <bool COMP>
+// when `maps` is given), else one CTA per tile.  INTER (pipelined kernel
+// only) also stores the intermediates the adjoint needs.
+template <bool COMP, bool INTER = false>
 inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a, bool pipe,
                                      int ctas, const TileMaps* maps) {
   using G = FusedGeom<FUSED_TX, FUSED_TY>;
   const int tcols = (a.nx + FUSED_TX - 1) / FUSED_TX, trows = (a.ny + FUSED_TY - 1) / FUSED_TY;
   if (pipe && ctas > 0 && pipe_eligible(a)) {
-    auto kern = k_fused_step_pipe<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
+    auto kern = k_fused_step_pipe<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP, INTER>;
     static bool configured = false;
     if (!configured) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -888,6 +918,7 @@ inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a, b
                                                                          maps ? 1 : 0);
     return cudaGetLastError();
   }
+  if (INTER) return cudaErrorNotSupported;
   auto kern = k_fused_step<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
   static bool configured = false;
   if (!configured) {

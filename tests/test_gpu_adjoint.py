@@ -114,3 +114,35 @@ def test_rollout_gradient_matches_finite_differences(precision, tol):
               _ke_after(P, P.state - eps * d, n_steps, "fp64")) / (2 * eps)
         ad = float(np.sum(g * d))
         assert abs(ad - fd) <= tol * max(abs(fd), 1e-12), (precision, trial, ad, fd)
+
+
+def _adjoint_with_env(P, lam, precision, env):
+    import os
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        s = af.Solver(P.grid, P.gamma, P.state, precision=precision)
+        out = s.adjoint(P.dt, lam)
+        s.close()
+        return out
+    finally:
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
+def test_fp32_adjoint_from_fused_intermediates(precision):
+    """On a grid the persistent fused kernel accepts, the FP32 adjoint recomputes
+    its intermediates with that kernel; it agrees with the FP64 adjoint to FP32
+    accuracy and with the FP32 adjoint built on the unfused intermediates."""
+    P = I.random_smooth(64, 48, seed=23, amp=0.05)
+    lam = np.random.default_rng(4).normal(size=P.state.shape)
+    fused = _adjoint_with_env(P, lam, precision, {})
+    unfused = _adjoint_with_env(P, lam, precision, {"AF_PIPE": "0"})
+    ref = _adjoint_with_env(P, lam, "fp64", {})
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(fused - ref)) / scale < 2e-5
+    assert np.max(np.abs(fused - unfused)) / scale < 2e-5
