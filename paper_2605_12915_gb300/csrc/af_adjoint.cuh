@@ -362,46 +362,59 @@ __device__ __forceinline__ void point_adj(const AdjView<T>& v, const Acc& acc, i
       lpP += -ly[0] * d[2] * rp / (gp * pp);
       ld[0] = ld[1] = ld[2] = T(0);
     }
-    // scatter through the Q2 evaluation at the foot and collect the adjoint of
-    // the foot's local coordinates
+    // adjoint of the foot's local coordinates through the Q2 evaluation there
     T lxi = T(0), leta = T(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const int n = 3 * b + q, fam = fam_of(q, b), cx = fc.ci + (q >> 1), cy = fc.cj + (b >> 1);
-        const T wgt = lx[q] * lyb[b];
-        acc.node(fam, cx, cy, wgt * lwf[0], wgt * lwf[1], wgt * lwf[2], wgt * lwf[3]);
+        const int n = 3 * b + q;
         T dot = nf[n].r * lwf[0] + nf[n].u * lwf[1] + nf[n].v * lwf[2] + nf[n].p * lwf[3];
-        if (v.variant == 0) {
-          acc.inc(s, fam, cx, cy, wgt * ld[0], wgt * ld[1], wgt * ld[2]);
-          dot += df[n][0] * ld[0] + df[n][1] * ld[1] + df[n][2] * ld[2];
-        }
+        if (v.variant == 0) dot += df[n][0] * ld[0] + df[n][1] * ld[1] + df[n][2] * ld[2];
         lxi += dx3[q] * lyb[b] * dot;
         leta += lx[q] * dy3[b] * dot;
       }
     // xi = 2 (foot - cell) - 1; the foot moved by df = -th (u1, v1)
-    const T ldfx = T(2) * lxi, ldfy = T(2) * leta;
-    const T lu1 = -th * ldfx, lv1 = -th * ldfy;
+    const T lu1 = -th * (T(2) * lxi), lv1 = -th * (T(2) * leta);
     // first Picard stage: (u1, v1) = R_h(u, v) at P + d1
-    lagrange3_d(c1.xi, dx3);
-    lagrange3_d(c1.eta, dy3);
-    lxi = T(0);
-    leta = T(0);
+    T dx31[3], dy31[3];
+    lagrange3_d(c1.xi, dx31);
+    lagrange3_d(c1.eta, dy31);
+    T lxi1 = T(0), leta1 = T(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const int n = 3 * b + q, fam = fam_of(q, b), cx = c1.ci + (q >> 1), cy = c1.cj + (b >> 1);
-        const T wgt = lx1[q] * ly1[b];
-        acc.node(fam, cx, cy, T(0), wgt * lu1, wgt * lv1, T(0));
+        const int n = 3 * b + q;
         const T dot = uv1[n][0] * lu1 + uv1[n][1] * lv1;
-        lxi += dx3[q] * ly1[b] * dot;
-        leta += lx1[q] * dy3[b] * dot;
+        lxi1 += dx31[q] * ly1[b] * dot;
+        leta1 += lx1[q] * dy31[b] * dot;
       }
-    const T ld1x = T(2) * lxi, ld1y = T(2) * leta;
-    luP += -th * ld1x;
-    lvP += -th * ld1y;
+    luP += -th * (T(2) * lxi1);
+    lvP += -th * (T(2) * leta1);
+    // scatter to the nodes of the foot cell and of the first stage's cell (one
+    // record update per node when the two cells coincide, the usual case)
+    const bool same = c1.ci == fc.ci && c1.cj == fc.cj;
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int fam = fam_of(q, b), cx = fc.ci + (q >> 1), cy = fc.cj + (b >> 1);
+        const T wgt = lx[q] * lyb[b], w1 = same ? lx1[q] * ly1[b] : T(0);
+        acc.node(fam, cx, cy, wgt * lwf[0], wgt * lwf[1] + w1 * lu1, wgt * lwf[2] + w1 * lv1,
+                 wgt * lwf[3]);
+        if (v.variant == 0) acc.inc(s, fam, cx, cy, wgt * ld[0], wgt * ld[1], wgt * ld[2]);
+      }
+    if (!same) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const T w1 = lx1[q] * ly1[b];
+          acc.node(fam_of(q, b), c1.ci + (q >> 1), c1.cj + (b >> 1), T(0), w1 * lu1, w1 * lv1,
+                   T(0));
+        }
+    }
   }
   acc.node(FAM, i, j, lrP, luP, lvP, lpP);
 }
