@@ -544,6 +544,20 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       // stored: the acoustically evolved velocity u + du, v + dv and the
       // pressure increment dp (the velocity increments are only ever added to
       // the interpolated velocity, so they are interpolated together with it)
+      // r-polynomial coefficients of (du, dv, dp), shared by both durations
+      // (the same operations as increments_at)
+      float cu[4], cv[4], cp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        cp[q] = fmaf(Z, Guv[0][q], Gp[0][q]);
+        cu[q] = fmaf(Zinv, Gp[1][q], Guv[1][q]);
+        cv[q] = fmaf(Zinv, Gp[2][q], Guv[2][q]);
+      }
+      auto horner = [&](float r, float d[3]) {
+        d[2] = r * fmaf(r, fmaf(r, fmaf(r, cp[3], cp[2]), cp[1]), cp[0]);
+        d[0] = r * fmaf(r, fmaf(r, fmaf(r, cu[3], cu[2]), cu[1]), cu[0]);
+        d[1] = r * fmaf(r, fmaf(r, fmaf(r, cv[3], cv[2]), cv[1]), cv[0]);
+      };
       float d[3];
       float* D0 = D + fam * 3 * DPL + dc;
       float* D1 = D + (4 + fam) * 3 * DPL + dc;
@@ -551,13 +565,13 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       const int gi = i0 - 1 + dx, gj = j0 - 1 + dy;
       const bool own = INTER && dx >= 1 && dx <= TX && dy >= 1 && dy <= TY && gi < nx && gj < ny;
       const size_t gid = own ? (size_t)gj * nx + gi : 0;
-      increments_at(Gp, Guv, Z, Zinv, 0.5f * r1, d);
+      horner(0.5f * r1, d);
       D0[0] = wk.y + d[0];
       D0[DPL] = wk.z + d[1];
       D0[2 * DPL] = d[2];
       if (own)
         for (int k = 0; k < 3; ++k) a.inc[0][fam][k][gid] = d[k];
-      increments_at(Gp, Guv, Z, Zinv, r1, d);
+      horner(r1, d);
       D1[0] = wk.y + d[0];
       D1[DPL] = wk.z + d[1];
       D1[2 * DPL] = d[2];

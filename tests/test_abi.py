@@ -47,14 +47,49 @@ def test_status_strings(libaf):
     assert libaf.af_status_string(9) == b"unknown status"
 
 
-def test_init_rejects_bad_arguments_without_touching_the_gpu(libaf):
+_BAD_INIT = {
+    "nx < 2": dict(nx=1),
+    "ny < 2": dict(ny=0),
+    "negative size": dict(nx=-8),
+    "h = 0": dict(h=0.0),
+    "h NaN": dict(h=float("nan")),
+    "gamma = 1": dict(gamma=1.0),
+    "gamma NaN": dict(gamma=float("nan")),
+    "unknown precision": dict(prec=3),
+    "unknown variant": dict(var=2),
+    "unknown memory kind": dict(where=2),
+    "null state plane": dict(null_plane=5),
+    "more than 2^31 cells": dict(nx=65536, ny=32769),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_BAD_INIT))
+def test_init_rejects_bad_arguments_without_touching_the_gpu(libaf, case):
+    """Every invalid argument is refused with AF_ERR_ARG before any CUDA call
+    (this runs on a machine without a GPU) and no handle is returned."""
     from paper_2605_12915_gb300 import AfGrid, AfState, AF_ERR_ARG
-    h = ctypes.c_void_p()
-    g = AfGrid(1, 4, 0.1)  # nx < 2
+    arg = dict(nx=16, ny=16, h=0.1, gamma=1.4, prec=0, var=0, where=0, null_plane=None)
+    arg.update(_BAD_INIT[case])
+    buf = (ctypes.c_double * 16)()
     st = AfState()
-    rc = libaf.af_init(ctypes.byref(h), ctypes.byref(g), ctypes.c_double(1.4), ctypes.byref(st),
-                       0, 0, 0, None)
+    for k, field in enumerate(("avg", "vtx", "ev", "eh")):
+        for q in range(4):
+            getattr(st, field)[q] = None if arg["null_plane"] == 4 * k + q else ctypes.addressof(buf)
+    h = ctypes.c_void_p()
+    g = AfGrid(arg["nx"], arg["ny"], arg["h"])
+    rc = libaf.af_init(ctypes.byref(h), ctypes.byref(g), ctypes.c_double(arg["gamma"]),
+                       ctypes.byref(st), arg["where"], arg["prec"], arg["var"], None)
     assert rc == AF_ERR_ARG and not h.value
+
+
+def test_calls_on_a_null_handle_are_refused(libaf):
+    from paper_2605_12915_gb300 import AF_ERR_ARG
+    libaf.af_step.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32]
+    assert libaf.af_step(None, ctypes.c_double(0.1), 1) == AF_ERR_ARG
+    libaf.af_sync.argtypes = [ctypes.c_void_p]
+    assert libaf.af_sync(None) == AF_ERR_ARG
+    libaf.af_destroy.argtypes = [ctypes.c_void_p]
+    libaf.af_destroy(None)  # a no-op
 
 
 @pytest.mark.slow
