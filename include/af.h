@@ -114,11 +114,14 @@ af_status af_step(af_handle *h, double dt, int32_t n_steps);
 af_status af_sync(af_handle *h);
 
 /* Copy the current state out as FP64 (AF_FP32_COMP: averages as hi + lo).
- * Synchronises the stream. */
+ * Synchronises the stream.  AF_HOST planes in pinned (page-locked) memory are
+ * written directly by the conversion kernel; pageable planes go through a
+ * device staging buffer and a copy. */
 af_status af_get_state(af_handle *h, const af_state_f64 *out, af_memory where);
 
 /* Replace the current state (converted to the handle's precision) and clear the
- * latched device error. */
+ * latched device error.  AF_HOST planes in pinned memory are read directly by
+ * the conversion kernel, pageable ones are copied first. */
 af_status af_set_state(af_handle *h, const af_state_f64 *in, af_memory where);
 
 /* FP64 global diagnostics of the current state, out[AF_NINV] in host memory.

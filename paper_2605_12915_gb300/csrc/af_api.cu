@@ -46,6 +46,7 @@ struct af_handle {
   int pipe_ctas;         // CTAs of the persistent pipelined fused kernel (0: off)
   TileMaps* tmaps;       // tensor maps of the input planes of state[0], state[1]
   int tma;               // 1: the pipelined kernel stages interior tiles by tensor copies
+  int zero_copy;         // 1: pinned host planes are converted in place (AF_ZERO_COPY=0: copies)
   void* adj_arena;       // adjoint arena (lazy): LAM_PLANES planes, see AdjView
 };
 
@@ -235,12 +236,32 @@ af_status cuda_fail(af_handle* h) {
   return AF_ERR_CUDA;
 }
 
+// Address under which the current device reaches the host plane p directly:
+// page-locked (pinned) host memory is mapped into the device's address space
+// and the import / export kernels read or write it in place over the
+// host-device link.  Null for pageable memory (only the copy engines may
+// touch it, through the staging buffer) or when the handle was created with
+// AF_ZERO_COPY=0.
+const void* mapped_host_plane(const af_handle* h, const void* p) {
+  if (!h->zero_copy) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 af_status import_state(af_handle* h, const af_state_f64* in, af_memory where) {
   F64Planes src;
   if (where == AF_HOST) {
-    af_status st = ensure_staging(h);
-    if (st != AF_OK) return st;
+    // pinned planes are read in place by the import kernel, pageable ones are
+    // copied to the staging buffer first
     for (int p = 0; p < 16; ++p) {
+      src.p[p] = (const double*)mapped_host_plane(h, plane_in(in, p));
+      if (src.p[p]) continue;
+      af_status st = ensure_staging(h);
+      if (st != AF_OK) return st;
       if (cudaMemcpyAsync(h->staging + (size_t)p * h->N, plane_in(in, p), sizeof(double) * h->N,
                           cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return cuda_fail(h);
@@ -417,6 +438,10 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
     const int cap = pp ? atoi(pp) : 0;
     h->pipe_ctas = !pp ? sms * AF_FUSED_MINB : (cap > 0 ? std::min(cap, sms * AF_FUSED_MINB) : 0);
   }
+  {
+    const char* zc = getenv("AF_ZERO_COPY");
+    h->zero_copy = (zc && zc[0] == '0') ? 0 : 1;
+  }
   // 2 x 20 state planes + 48 scratch planes, each padded to 256 bytes
   size_t plane = (h->N * h->esize + 255) & ~(size_t)255;
   size_t nplanes = 2 * 20 + 48;
@@ -526,10 +551,18 @@ af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
   F64Out dst;
+  bool copy_back[16] = {};
   if (where == AF_HOST) {
-    af_status st = ensure_staging(h);
-    if (st != AF_OK) return st;
-    for (int p = 0; p < 16; ++p) dst.p[p] = h->staging + (size_t)p * h->N;
+    // pinned planes are written in place by the export kernel, pageable ones
+    // through the staging buffer
+    for (int p = 0; p < 16; ++p) {
+      dst.p[p] = (double*)mapped_host_plane(h, plane_in(out, p));
+      if (dst.p[p]) continue;
+      af_status st = ensure_staging(h);
+      if (st != AF_OK) return st;
+      dst.p[p] = h->staging + (size_t)p * h->N;
+      copy_back[p] = true;
+    }
   } else {
     for (int p = 0; p < 16; ++p) dst.p[p] = (double*)plane_in(out, p);
   }
@@ -540,12 +573,11 @@ af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
     case AF_FP32_COMP: k_export<float, true><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N, offsets_of(h)); break;
   }
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
-  if (where == AF_HOST) {
-    for (int p = 0; p < 16; ++p)
-      if (cudaMemcpyAsync((void*)plane_in(out, p), dst.p[p], sizeof(double) * h->N,
-                          cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
-        return cuda_fail(h);
-  }
+  for (int p = 0; p < 16; ++p)
+    if (copy_back[p] &&
+        cudaMemcpyAsync((void*)plane_in(out, p), dst.p[p], sizeof(double) * h->N,
+                        cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+      return cuda_fail(h);
   return af_sync(h);
 }
 

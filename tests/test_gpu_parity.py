@@ -241,6 +241,43 @@ def test_pipelined_fp32_matches_oracle_random(orc, variant):
     assert rel_linf(got, want) < TOL32
 
 
+def test_state_transfer_pinned_pageable_and_device_agree():
+    """Pinned host planes are read and written in place by the conversion
+    kernels, pageable ones through the staging copy; both give the same bits
+    as device buffers (and AF_ZERO_COPY=0 forces the copies)."""
+    import torch
+    P = I.random_smooth(72, 40, seed=31, amp=0.06)
+    for precision in ("fp64", "fp32_comp"):
+        outs = []
+        for kind in ("numpy", "pinned", "device", "copies"):
+            def run():
+                if kind == "numpy":
+                    src = P.state.copy()
+                elif kind == "pinned":
+                    src = torch.from_numpy(P.state.copy()).pin_memory()
+                else:
+                    src = torch.from_numpy(P.state.copy()).cuda()
+                s = af.Solver(P.grid, P.gamma, src, precision=precision)
+                s.step(P.dt, 3)
+                s.set_state(src)
+                s.step(P.dt, 3)
+                if kind == "pinned":
+                    out = torch.empty(P.state.shape, dtype=torch.float64).pin_memory()
+                    s.state(out)
+                    out = out.numpy()
+                elif kind == "device":
+                    out = torch.empty(P.state.shape, dtype=torch.float64, device="cuda")
+                    s.state(out)
+                    out = out.cpu().numpy()
+                else:
+                    out = s.state()
+                s.close()
+                return out
+            outs.append(_with_env("AF_ZERO_COPY", "0", run) if kind == "copies" else run())
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o), precision
+
+
 def test_fused_conservation_and_determinism():
     P = I.random_smooth(130, 70, seed=6, amp=0.05)
     s = af.Solver(P.grid, P.gamma, P.state, precision="fp32_comp")
