@@ -416,8 +416,9 @@ def adjoint_cost(af, P, args, stream, torch, fwd_ms):
     s.close()
     ms = e0.elapsed_time(e1) / args.adjoint_steps
     return {"ms_per_step": ms, "forward_ms_per_step": fwd_ms, "ratio": ms / fwd_ms,
-            "note": "adjoint recomputes the step's intermediates with the unfused kernels and "
-                    "includes FP64 conversion of the adjoint state in and out"}
+            "note": "adjoint step = recomputation of the step's intermediates (fused kernel in "
+                    "the FP32 modes) + reverse sweep, including the FP64 conversion of the "
+                    "adjoint state in and out"}
 
 
 def solver_state_after(af, P, args, stream):
