@@ -16,6 +16,7 @@
 #include "af_reduce.cuh"
 #include "af_ref_kernels.cuh"
 #include "af_fused.cuh"
+#include "af_launch.cuh"
 #include "af_adjoint.cuh"
 
 using namespace af;

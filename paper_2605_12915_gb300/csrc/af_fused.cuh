@@ -864,120 +864,4 @@ __global__ void __launch_bounds__(NT, MINB)
 
 constexpr int FUSED_TX = AF_FUSED_TX, FUSED_TY = AF_FUSED_TY, FUSED_NT = AF_FUSED_NT;
 
-// The pipelined kernel's conditions on the grid and the input planes.
-inline bool pipe_eligible(const StepArgs<float>& a) {
-  if ((a.nx & 3) != 0 || a.nx < FUSED_TX + 8 || a.ny < FUSED_TY + 6) return false;
-  uintptr_t bits = 0;
-  for (int q = 0; q < 4; ++q) bits |= (uintptr_t)a.in.avg[q] | (uintptr_t)a.in.lo[q];
-  for (int f = 0; f < 3; ++f)
-    for (int k = 0; k < 4; ++k) bits |= (uintptr_t)a.in.pt[f][k];
-  return (bits & 15) == 0;
-}
-
-// Encodes the tensor maps of the 20 input planes in `a` (row-major nx x ny
-// floats, staging box of the fused tile geometry); false if the driver lacks the
-// encoder or rejects a map.
-inline bool encode_tile_maps(const StepArgs<float>& a, TileMaps* out) {
-  typedef CUresult (*Encode)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                             const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                             const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                             CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static Encode enc = nullptr;
-  if (!enc) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-      cudaGetLastError();
-      return false;
-    }
-    enc = (Encode)fn;
-  }
-  using G = FusedGeom<FUSED_TX, FUSED_TY>;
-  const cuuint64_t dims[2] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny};
-  const cuuint64_t strides[1] = {(cuuint64_t)a.nx * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)G::SW, (cuuint32_t)G::CH}, unit[2] = {1, 1};
-  for (int p = 0; p < 20; ++p) {
-    float* base = p < 12 ? a.in.pt[p >> 2][p & 3] : p < 16 ? a.in.avg[p - 12] : a.in.lo[p - 16];
-    if (enc(&out->m[p], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, unit,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return false;
-  }
-  return true;
-}
-
-// One step of the grid described by `a`: the persistent pipelined kernel on
-// `ctas` CTAs when `pipe` is set and the grid allows it (tensor-copy staging
-// when `maps` is given), else one CTA per tile.  INTER (pipelined kernel
-// only) also stores the intermediates the adjoint needs.
-template <bool COMP, bool INTER = false>
-inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a, bool pipe,
-                                     int ctas, const TileMaps* maps) {
-  using G = FusedGeom<FUSED_TX, FUSED_TY>;
-  const int tcols = (a.nx + FUSED_TX - 1) / FUSED_TX, trows = (a.ny + FUSED_TY - 1) / FUSED_TY;
-  if (pipe && ctas > 0 && pipe_eligible(a)) {
-    auto kern = k_fused_step_pipe<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP, INTER>;
-    static bool configured = false;
-    if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)G::SMEM_PIPE);
-      if (e != cudaSuccess) return e;
-      configured = true;
-    }
-    static TileMaps none;
-    const int ntiles = tcols * trows;
-    kern<<<ntiles < ctas ? ntiles : ctas, FUSED_NT, G::SMEM_PIPE, s>>>(a, maps ? *maps : none,
-                                                                         maps ? 1 : 0);
-    return cudaGetLastError();
-  }
-  if (INTER) return cudaErrorNotSupported;
-  auto kern = k_fused_step<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  dim3 grd(tcols, trows);
-  kern<<<grd, FUSED_NT, G::SMEM, s>>>(a);
-  return cudaGetLastError();
-}
-
-// Tile geometries available to the batched launch (the autotuner picks one).
-struct BatchGeometry {
-  int tx, ty, nt, minb;
-};
-constexpr int N_BATCH_GEOMS = 3;
-constexpr BatchGeometry BATCH_GEOMS[N_BATCH_GEOMS] = {{32, 32, 512, 1}, {24, 16, 256, 2},
-                                                      {16, 16, 256, 3}};
-
-template <int TX, int TY, int NT, int MINB, bool COMP>
-inline cudaError_t launch_batch_geom(cudaStream_t s, const StepArgs<float>* args,
-                                     const int4* tiles, int ntiles) {
-  using G = FusedGeom<TX, TY>;
-  auto kern = k_fused_step_batch<TX, TY, NT, MINB, COMP>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  kern<<<ntiles, NT, G::SMEM, s>>>(args, tiles);
-  return cudaGetLastError();
-}
-
-template <bool COMP>
-inline cudaError_t launch_batch(int geom, cudaStream_t s, const StepArgs<float>* args,
-                                const int4* tiles, int ntiles) {
-  switch (geom) {
-    case 0: return launch_batch_geom<32, 32, 512, 1, COMP>(s, args, tiles, ntiles);
-    case 1: return launch_batch_geom<24, 16, 256, 2, COMP>(s, args, tiles, ntiles);
-    default: return launch_batch_geom<16, 16, 256, 3, COMP>(s, args, tiles, ntiles);
-  }
-}
-
 }  // namespace af
