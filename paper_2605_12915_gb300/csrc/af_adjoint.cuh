@@ -17,6 +17,8 @@
 #pragma once
 
 #include "af_common.cuh"
+#include "af_fused.cuh"
+#include "af_launch.cuh"
 #include "af_ref_kernels.cuh"
 
 namespace af {
@@ -573,6 +575,255 @@ __global__ void k_adj_center(const __grid_constant__ AdjView<T> v) {
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Fused reverse sweep of a tile (FP32 modes).  fused_tile<..., ADJ> leaves the
+// tile's time-n nodes W and the increments D of both durations in shared
+// memory.  For each owned point: the adjoint of the space-time Simpson fluxes
+// it enters (gathered from the averages' lambda, as k_adj_flux), then the
+// adjoint of its point update for both durations (as k_adj_points) with the
+// forward values taken from shared memory and the foot traced as the fused
+// step traces it (displacements clamped to one cell).  Results go to the node
+// and increment records (float4 atomics); the averages' lambda passes through.
+// ---------------------------------------------------------------------------
+template <int TX, int TY, int NT>
+__device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const AdjView<float>& v,
+                                             const float4* W, const float* D, int i0, int j0) {
+  using G = FusedGeom<TX, TY>;
+  constexpr int CW = G::CW, WPL = G::WPL, DCW = G::DCW, DPL = G::DPL;
+  const int nx = a.nx, ny = a.ny;
+  const size_t ps = v.ps;
+  const Gas<float> gas = a.gas;
+  const VecAdj<float> acc = vec_adj(v);
+  const float th_full = a.dt / a.h;
+  const float cst = a.dt / (36.f * a.h);
+  const float* lin = v.lam + (size_t)LAM_IN * ps;
+  for (int t = threadIdx.x; t < 3 * TX * TY; t += NT) {
+    const int fam = t / (TX * TY), u = t - fam * (TX * TY);
+    const int px = u % TX, py = u / TX;
+    const int gi = i0 + px, gj = j0 + py;
+    if (gi >= nx || gj >= ny) continue;
+    const size_t id = (size_t)gj * nx + gi;
+    // ---- fluxes (Eq. af-average-update), reversed ----
+    const int im = wrapc(gi - 1, nx), jm = wrapc(gj - 1, ny);
+    const size_t idl = (size_t)gj * nx + im, idb = (size_t)jm * nx + gi,
+                 idlb = (size_t)jm * nx + im;
+    float lex[4], ley[4];  // adjoints of the x- and y-fluxes the point enters
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float* lk = lin + (size_t)k * ps;
+      const float c = lk[id], l = lk[idl], b = lk[idb], lb = lk[idlb];
+      lex[k] = fam == 0 ? (c - l) + (b - lb) : c - l;
+      ley[k] = fam == 0 ? (c - b) + (l - lb) : c - b;
+      if (fam == 0) v.lam[(size_t)(LAM_OUT + k) * ps + id] = c;
+    }
+    const int wcP = (py + 2) * CW + (px + 2);
+    const float4 wp = W[fam * WPL + wcP];
+    float o0[4], lyh[4], lyf[4];  // sigma = 0 (own node), 1/2 and 1 (the point)
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      Prim<float> w;
+      if (s == 0) {
+        w = prim4(wp);
+      } else {
+        float* const* src = s == 1 ? a.half[fam] : a.out.pt[fam];
+        w.r = src[0][id];
+        w.u = src[1][id];
+        w.v = src[2][id];
+        w.p = src[3][id];
+      }
+      const float sc = cst * (s == 1 ? 4.f : 1.f);
+      float o[4] = {0.f, 0.f, 0.f, 0.f};
+      if (fam == 0) {
+        flux_x_adj(w, gas, lex, sc, o);
+        flux_y_adj(w, gas, ley, sc, o);
+      } else if (fam == 1) {
+        flux_x_adj(w, gas, lex, 4.f * sc, o);
+      } else {
+        flux_y_adj(w, gas, ley, 4.f * sc, o);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (s == 0) o0[k] = o[k];
+        else if (s == 1) lyh[k] = o[k];
+        else lyf[k] = o[k] + lin[(size_t)(4 + 4 * fam + k) * ps + id];
+      }
+    }
+    // ---- point update (Sec. 6.1 steps 3-4), reversed, both durations ----
+    const int ox = fam == 2 ? 1 : 0, oy = fam == 1 ? 1 : 0;
+    float luP = 0.f, lvP = 0.f, lrP = 0.f, lpP = 0.f;
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+      const float th = s == 0 ? 0.5f * th_full : th_full;
+      const float* Ds = D + s * 12 * DPL;
+      float ly[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ly[k] = s == 0 ? lyh[k] : lyf[k];
+      // forward: the two Picard stages as the fused step traces them
+      const float d1x = clamp1(-th * wp.y), d1y = clamp1(-th * wp.z);
+      float lx1[3], ly1[3];
+      const int ix1 = foot_axis(ox, d1x, lx1), iy1 = foot_axis(oy, d1y, ly1);
+      const int c1 = wcP + iy1 * CW + ix1;
+      float4 n[9];
+      load_cell<CW, WPL>(W, c1, n);
+      const float u1 = AF_Q2(n, y, lx1, ly1), v1 = AF_Q2(n, z, lx1, ly1);
+      const float dfx = clamp1(-th * u1), dfy = clamp1(-th * v1);
+      float lx[3], lyb[3];
+      const int ix = foot_axis(ox, dfx, lx), iy = foot_axis(oy, dfy, lyb);
+      const int c2 = wcP + iy * CW + ix;
+      if (c2 != c1) load_cell<CW, WPL>(W, c2, n);
+      const float rft = AF_Q2(n, x, lx, lyb), pft = AF_Q2(n, w, lx, lyb);
+      // local coordinates of the foot and of the first stage
+      float dx3[3], dy3[3], dx31[3], dy31[3];
+      {
+        const float fx = fmaf(0.5f, (float)ox, dfx), fy = fmaf(0.5f, (float)oy, dfy);
+        lagrange3_d(2.f * (fx - floorf(fx)) - 1.f, dx3);
+        lagrange3_d(2.f * (fy - floorf(fy)) - 1.f, dy3);
+        const float gx = fmaf(0.5f, (float)ox, d1x), gy = fmaf(0.5f, (float)oy, d1y);
+        lagrange3_d(2.f * (gx - floorf(gx)) - 1.f, dx31);
+        lagrange3_d(2.f * (gy - floorf(gy)) - 1.f, dy31);
+      }
+      const int dcf = (py + 1 + iy) * DCW + (px + 1 + ix);  // D cell of the foot cell
+      float lwf[4], ld[3];  // adjoints of W at the foot and of the interpolated increments
+      if (a.variant == 0) {
+        const float d2 = q2_eval<DCW>(Ds + 2 * DPL, Ds + 5 * DPL, Ds + 8 * DPL, Ds + 11 * DPL,
+                                      dcf, lx, lyb);
+        const float rf = gas.rho_ref + rft, pf = gas.p_ref + pft, gp = gas.gamma * pf;
+        lwf[0] = ly[0] * (1.f + d2 / gp);
+        lwf[1] = ly[1];
+        lwf[2] = ly[2];
+        lwf[3] = ly[3] - ly[0] * d2 * rf / (gp * pf);
+        ld[0] = ly[1];
+        ld[1] = ly[2];
+        ld[2] = ly[3] + ly[0] * rf / gp;
+      } else {
+        const int dcp = (py + 1) * DCW + (px + 1);
+        const float d2 = Ds[(fam * 3 + 2) * DPL + dcp];
+        const float rp = gas.rho_ref + wp.x, pp = gas.p_ref + wp.w, gp = gas.gamma * pp;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) lwf[k] = ly[k];
+        // rho = rho_f + dp rho_P / (gamma p_P), with the increments at P itself
+        acc.inc(s, fam, gi, gj, ly[1], ly[2], ly[3] + ly[0] * rp / gp);
+        lrP += ly[0] * d2 / gp;
+        lpP += -ly[0] * d2 * rp / (gp * pp);
+        ld[0] = ld[1] = ld[2] = 0.f;
+      }
+      // adjoint of the foot's local coordinates.  D holds (u + du, v + dv, dp);
+      // u and du enter the transported update with the same weight.
+      float lxi = 0.f, leta = 0.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int m = 3 * b + q, fn = fam_of(q, b);
+          float dot;
+          if (a.variant == 0) {
+            const int dn = dcf + (b >> 1) * DCW + (q >> 1);
+            dot = n[m].x * lwf[0] + Ds[(fn * 3) * DPL + dn] * lwf[1] +
+                  Ds[(fn * 3 + 1) * DPL + dn] * lwf[2] + n[m].w * lwf[3] +
+                  Ds[(fn * 3 + 2) * DPL + dn] * ld[2];
+          } else {
+            dot = n[m].x * lwf[0] + n[m].y * lwf[1] + n[m].z * lwf[2] + n[m].w * lwf[3];
+          }
+          lxi += dx3[q] * lyb[b] * dot;
+          leta += lx[q] * dy3[b] * dot;
+        }
+      // xi = 2 (foot - cell) - 1; the foot moved by df = -th (u1, v1)
+      const float lu1 = -th * (2.f * lxi), lv1 = -th * (2.f * leta);
+      // first Picard stage: (u1, v1) = R_h(u, v) at P + d1
+      if (c2 != c1) load_cell<CW, WPL>(W, c1, n);
+      float lxi1 = 0.f, leta1 = 0.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int m = 3 * b + q;
+          const float dot = n[m].y * lu1 + n[m].z * lv1;
+          lxi1 += dx31[q] * ly1[b] * dot;
+          leta1 += lx1[q] * dy31[b] * dot;
+        }
+      luP += -th * (2.f * lxi1);
+      lvP += -th * (2.f * leta1);
+      // scatter to the foot cell's nodes (and the first stage's, merged when
+      // both use the same cell)
+      const bool same = c1 == c2;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int fn = fam_of(q, b), cx = gi + ix + (q >> 1), cy = gj + iy + (b >> 1);
+          const float wgt = lx[q] * lyb[b], w1 = same ? lx1[q] * ly1[b] : 0.f;
+          acc.node(fn, cx, cy, wgt * lwf[0], fmaf(w1, lu1, wgt * lwf[1]),
+                   fmaf(w1, lv1, wgt * lwf[2]), wgt * lwf[3]);
+          if (a.variant == 0) acc.inc(s, fn, cx, cy, wgt * ld[0], wgt * ld[1], wgt * ld[2]);
+        }
+      if (!same) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float w1 = lx1[q] * ly1[b];
+            acc.node(fam_of(q, b), gi + ix1 + (q >> 1), gj + iy1 + (b >> 1), 0.f, w1 * lu1,
+                     w1 * lv1, 0.f);
+          }
+      }
+    }
+    acc.node(fam, gi, gj, o0[0] + lrP, o0[1] + luP, o0[2] + lvP, o0[3] + lpP);
+  }
+}
+
+// Persistent kernel of the fused reverse sweep: the pipelined step's tile loop
+// (k_fused_step_pipe) with fused_tile<..., ADJ> and tile_reverse per tile; the
+// next tile's input is staged once the reverse sweep is done with D.
+template <int TX, int TY, int NT, int MINB, bool COMP>
+__global__ void __launch_bounds__(NT, MINB)
+    k_fused_adj_pipe(const __grid_constant__ StepArgs<float> a, const __grid_constant__ TileMaps tm,
+                     int use_tma, const __grid_constant__ AdjView<float> v) {
+  using G = FusedGeom<TX, TY>;
+  extern __shared__ __align__(16) float4 smem4[];
+  float* S = reinterpret_cast<float*>(smem4 + 4 * G::WPL);
+  PipeCtx pc;
+  pc.tm = (use_tma && G::W_BYTES % 128 == 0 && (smem_addr(smem4) & 127u) == 0) ? &tm : nullptr;
+  pc.bar = smem_addr(reinterpret_cast<char*>(smem4) + G::SMEM);
+  pc.phase = 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pc.bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int tcols = (a.nx + TX - 1) / TX, ntiles = tcols * ((a.ny + TY - 1) / TY);
+  int tile = blockIdx.x;
+  if (tile < ntiles)
+    issue_tile_async<TX, TY, NT, COMP>(a, pc, (tile % tcols) * TX, (tile / tcols) * TY, S);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int nxt = tile + gridDim.x;
+    const int pi0 = nxt < ntiles ? (nxt % tcols) * TX : -1, pj0 = (nxt / tcols) * TY;
+    const int i0 = (tile % tcols) * TX, j0 = (tile / tcols) * TY;
+    if (!fused_tile<TX, TY, NT, COMP, true, false, true>(a, pc, i0, j0, pi0, pj0,
+                                                         a.prefetch_wave > 0 && !pc.tm))
+      break;
+    tile_reverse<TX, TY, NT>(a, v, smem4, S, i0, j0);
+    __syncthreads();  // W and D are dead from here
+    if (pi0 >= 0) issue_tile_async<TX, TY, NT, COMP>(a, pc, pi0, pj0, S);
+  }
+}
+
+// Launches the fused reverse sweep when the pipelined kernel accepts the grid
+// (cudaErrorNotSupported otherwise).
+template <bool COMP>
+inline cudaError_t launch_fused_adjoint(cudaStream_t s, const StepArgs<float>& a, int ctas,
+                                        const TileMaps* maps, const AdjView<float>& v) {
+  using G = FusedGeom<FUSED_TX, FUSED_TY>;
+  if (!(ctas > 0 && pipe_eligible(a))) return cudaErrorNotSupported;
+  constexpr auto kern = k_fused_adj_pipe<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
+  const cudaError_t e = allow_smem<kern>(G::SMEM_PIPE);
+  if (e != cudaSuccess) return e;
+  static TileMaps none;
+  const int ntiles = ((a.nx + FUSED_TX - 1) / FUSED_TX) * ((a.ny + FUSED_TY - 1) / FUSED_TY);
+  kern<<<ntiles < ctas ? ntiles : ctas, FUSED_NT, G::SMEM_PIPE, s>>>(a, maps ? *maps : none,
+                                                                       maps ? 1 : 0, v);
+  return cudaGetLastError();
 }
 
 // Sixteen planes converted in one launch (the adjoint state in and out).

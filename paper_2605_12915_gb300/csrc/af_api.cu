@@ -327,10 +327,39 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
     cin.dst[p] = v.lam + (size_t)(LAM_IN + p) * v.ps;
   }
   k_cast16<<<grid1d(h->N), 256, 0, s>>>(cin, h->N);
+  dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
+  // FP32 modes on grids the pipelined kernel accepts: one fused launch
+  // recomputes each tile's step in shared memory and reverses its fluxes and
+  // point updates there (AF_ADJ_FUSED=0 selects the kernel-per-stage sweep)
+  if constexpr (std::is_same<T, float>::value) {
+    const char* fz = getenv("AF_ADJ_FUSED");
+    if (h->fused && h->pipe_ctas > 0 && pipe_eligible(f) && !(fz && fz[0] == '0')) {
+      // node and increment records start at zero (planes LAM_NODE ... LAM_INC + 31)
+      if (cudaMemsetAsync(v.lam + (size_t)LAM_NODE * v.ps, 0, plane * 48, s) != cudaSuccess ||
+          launch_fused_adjoint<COMP>(s, f, h->pipe_ctas, h->tma ? &h->tmaps[h->cur] : nullptr,
+                                     v) != cudaSuccess)
+        return cuda_fail(h);
+      k_adj_acoustic<0, T><<<grd, blk, 0, s>>>(v);
+      k_adj_acoustic<1, T><<<grd, blk, 0, s>>>(v);
+      k_adj_acoustic<2, T><<<grd, blk, 0, s>>>(v);
+      k_adj_acoustic<3, T><<<grd, blk, 0, s>>>(v);
+      k_adj_center<T><<<grd, blk, 0, s>>>(v);
+      AdjOut<T> out;
+      for (int p = 0; p < 16; ++p)
+        out.dst[p] = where == AF_HOST ? h->staging + (size_t)p * h->N : (double*)plane_in(lout, p);
+      k_adj_out<T><<<grid1d(h->N), 256, 0, s>>>(v, out, h->N);
+      if (where == AF_HOST)
+        for (int p = 0; p < 16; ++p)
+          if (cudaMemcpyAsync((void*)plane_in(lout, p), h->staging + (size_t)p * h->N,
+                              sizeof(double) * h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return cuda_fail(h);
+      if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+      return af_sync(h);
+    }
+  }
   // forward intermediates of the step from the handle's current state: the
   // pipelined fused kernel stores them where it runs (FP32 modes), else the
   // unfused kernels
-  dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
   bool fused_inter = false;
   if constexpr (std::is_same<T, float>::value) {
     if (h->fused && h->pipe_ctas > 0 && pipe_eligible(f)) {

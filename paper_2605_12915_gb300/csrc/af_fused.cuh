@@ -344,8 +344,10 @@ __device__ __forceinline__ void issue_tile_async(const StepArgs<float>& a, const
 // (issue_tile_async); false means the wait for it timed out (flagged).  With
 // INTER the tile also stores the intermediates of its owned cells that the
 // adjoint linearises about: centres (a.wc), increments (a.inc) and half-step
-// points (a.half).
-template <int TX, int TY, int NT, bool COMP, bool PIPE, bool INTER = false>
+// points (a.half).  With ADJ it stores the centres and half-step points, keeps
+// the increments D in shared memory (the points are not written over them) and
+// returns after the point updates, for the adjoint's reverse sweep of the tile.
+template <int TX, int TY, int NT, bool COMP, bool PIPE, bool INTER = false, bool ADJ = false>
 __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc, int i0, int j0,
                                            int pi0, int pj0, bool pf) {
   using G = FusedGeom<TX, TY>;
@@ -495,7 +497,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     const Prim<float> w = stored_from_cons_inv(uc, gas, __fdividef(1.f, gas.rho_ref + uc[0]));
     if (!(gas.rho_ref + w.r > 0.f && gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
     W[3 * WPL + c] = make_float4(w.r, w.u, w.v, w.p);
-    if constexpr (INTER) {
+    if constexpr (INTER || ADJ) {
       const int gi = i0 - 2 + cx, gj = j0 - 2 + cy;
       if (cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2 && gi < nx && gj < ny) {
         const size_t id = (size_t)gj * nx + gi;
@@ -651,7 +653,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       res[k] = make_float4(nw.r, nw.u, nw.v, nw.p);
       // owned points at t^{n+1} go straight to HBM
       const int gi = i0 + px, gj = j0 + py;
-      if (INTER && s == 0 && px < TX && py < TY && gi < nx && gj < ny) {
+      if ((INTER || ADJ) && s == 0 && px < TX && py < TY && gi < nx && gj < ny) {
         const size_t id = (size_t)gj * nx + gi;
         a.half[fam][0][id] = nw.r;
         a.half[fam][1][id] = nw.u;
@@ -666,18 +668,24 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
         a.out.pt[fam][3][id] = nw.p;
       }
     }
-    __syncthreads();  // D(s) is dead from here
-    float4* P = reinterpret_cast<float4*>(D + s * 12 * DPL);
+    __syncthreads();  // D(s) is dead from here (except for ADJ)
+    if constexpr (!ADJ) {
+      float4* P = reinterpret_cast<float4*>(D + s * 12 * DPL);
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int t = threadIdx.x + k * NT;
-      if (t >= NPTS) break;
-      int fam, px, py;
-      point_item<PW, G::PH>(t, fam, px, py);
-      P[fam * PPL + py * PW + px] = res[k];
+      for (int k = 0; k < PER; ++k) {
+        const int t = threadIdx.x + k * NT;
+        if (t >= NPTS) break;
+        int fam, px, py;
+        point_item<PW, G::PH>(t, fam, px, py);
+        P[fam * PPL + py * PW + px] = res[k];
+      }
     }
   }
   __syncthreads();
+  if constexpr (ADJ) {
+    if (bad) atomicOr(a.flags, bad);
+    return true;
+  }
 
   // ---- phase 4: space-time Simpson fluxes (Sec. 3.1) and average update -------
   // vertical edges (i0+ex, j0+ey), ex in [0, TX], ey in [0, TY); horizontal edges

@@ -116,13 +116,13 @@ def test_rollout_gradient_matches_finite_differences(precision, tol):
         assert abs(ad - fd) <= tol * max(abs(fd), 1e-12), (precision, trial, ad, fd)
 
 
-def _adjoint_with_env(P, lam, precision, env):
+def _adjoint_with_env(P, lam, precision, env, variant="tai", dt=None):
     import os
     old = {k: os.environ.get(k) for k in env}
     os.environ.update(env)
     try:
-        s = af.Solver(P.grid, P.gamma, P.state, precision=precision)
-        out = s.adjoint(P.dt, lam)
+        s = af.Solver(P.grid, P.gamma, P.state, precision=precision, variant=variant)
+        out = s.adjoint(P.dt if dt is None else dt, lam)
         s.close()
         return out
     finally:
@@ -134,15 +134,24 @@ def _adjoint_with_env(P, lam, precision, env):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
-def test_fp32_adjoint_from_fused_intermediates(precision):
-    """On a grid the persistent fused kernel accepts, the FP32 adjoint recomputes
-    its intermediates with that kernel; it agrees with the FP64 adjoint to FP32
-    accuracy and with the FP32 adjoint built on the unfused intermediates."""
-    P = I.random_smooth(64, 48, seed=23, amp=0.05)
+@pytest.mark.parametrize("variant", ["tai", "rb"])
+@pytest.mark.parametrize("shape,ctas", [((64, 48), None), ((200, 168), "3")])
+def test_fp32_adjoint_paths_match_fp64_adjoint(precision, variant, shape, ctas):
+    """The FP32 adjoint on grids the persistent fused kernel accepts: the fused
+    reverse sweep (each tile's step recomputed and its fluxes and point updates
+    reversed in shared memory), the kernel-per-stage sweep on the fused
+    kernel's stored intermediates (AF_ADJ_FUSED=0) and the unfused path
+    (AF_PIPE=0) all agree with the FP64 adjoint to FP32 accuracy.  200 x 168
+    on three CTAs steps each CTA through fourteen tiles, some staged by tensor
+    copies."""
+    nx, ny = shape
+    P = I.random_smooth(nx, ny, seed=23 + nx, amp=0.05)
+    dt = P.dt * (0.6 if variant == "rb" else 1.0)
     lam = np.random.default_rng(4).normal(size=P.state.shape)
-    fused = _adjoint_with_env(P, lam, precision, {})
-    unfused = _adjoint_with_env(P, lam, precision, {"AF_PIPE": "0"})
-    ref = _adjoint_with_env(P, lam, "fp64", {})
+    env = {"AF_PIPE": ctas} if ctas else {}
+    ref = _adjoint_with_env(P, lam, "fp64", {}, variant, dt)
     scale = np.max(np.abs(ref))
-    assert np.max(np.abs(fused - ref)) / scale < 2e-5
-    assert np.max(np.abs(fused - unfused)) / scale < 2e-5
+    for name, e in (("fused", env), ("staged", dict(env, AF_ADJ_FUSED="0")),
+                    ("unfused", {"AF_PIPE": "0"})):
+        got = _adjoint_with_env(P, lam, precision, e, variant, dt)
+        assert np.max(np.abs(got - ref)) / scale < 2e-5, name
