@@ -599,10 +599,14 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
   const float th_full = a.dt / a.h;
   const float cst = a.dt / (36.f * a.h);
   const float* lin = v.lam + (size_t)LAM_IN * ps;
+  static_assert(TX == 32 && (3 * TX * TY) % NT == 0, "a warp is one row of one family");
+  const int lane = threadIdx.x & 31;
   for (int t = threadIdx.x; t < 3 * TX * TY; t += NT) {
     const int fam = t / (TX * TY), u = t - fam * (TX * TY);
     const int px = u % TX, py = u / TX;
     const int gi = i0 + px, gj = j0 + py;
+    // lanes of the warp inside the grid (every lane of the warp is here)
+    const unsigned mask = __ballot_sync(0xffffffffu, gi < nx && gj < ny);
     if (gi >= nx || gj >= ny) continue;
     const size_t id = (size_t)gj * nx + gi;
     // ---- fluxes (Eq. af-average-update), reversed ----
@@ -746,18 +750,59 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
       luP += -th * (2.f * lxi1);
       lvP += -th * (2.f * leta1);
       // scatter to the foot cell's nodes (and the first stage's, merged when
-      // both use the same cell)
+      // both use the same cell).  When the right-hand neighbour lane (the next
+      // point of the row) has its foot at the same offset, its first node
+      // column is this lane's last: it hands those contributions over and this
+      // lane adds them with its own (one record update instead of two).
       const bool same = c1 == c2;
+      // wrapped cells of the foot cell's 2 x 2 block of node cells
+      const int col0 = wrapc(gi + ix, nx), col1 = col0 + 1 == nx ? 0 : col0 + 1;
+      const size_t row0 = (size_t)wrapc(gj + iy, ny) * nx;
+      const size_t row1 = (row0 + nx == (size_t)ny * nx) ? 0 : row0 + nx;
+      const int key = (ix + 2) + 8 * (iy + 2);
+      const int lkey = __shfl_up_sync(mask, key, 1), rkey = __shfl_down_sync(mask, key, 1);
+      const bool give = lane > 0 && ((mask >> (lane - 1)) & 1u) && lkey == key;
+      const bool take = lane < 31 && ((mask >> (lane + 1)) & 1u) && rkey == key;
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
+      for (int b = 0; b < 3; ++b) {
+        float nd[3][4], ic[3][3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const int fn = fam_of(q, b), cx = gi + ix + (q >> 1), cy = gj + iy + (b >> 1);
           const float wgt = lx[q] * lyb[b], w1 = same ? lx1[q] * ly1[b] : 0.f;
-          acc.node(fn, cx, cy, wgt * lwf[0], fmaf(w1, lu1, wgt * lwf[1]),
-                   fmaf(w1, lv1, wgt * lwf[2]), wgt * lwf[3]);
-          if (a.variant == 0) acc.inc(s, fn, cx, cy, wgt * ld[0], wgt * ld[1], wgt * ld[2]);
+          nd[q][0] = wgt * lwf[0];
+          nd[q][1] = fmaf(w1, lu1, wgt * lwf[1]);
+          nd[q][2] = fmaf(w1, lv1, wgt * lwf[2]);
+          nd[q][3] = wgt * lwf[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) ic[q][k] = wgt * ld[k];
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float r = __shfl_down_sync(mask, nd[0][k], 1);
+          if (take) nd[2][k] += r;
+        }
+        if (a.variant == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float r = __shfl_down_sync(mask, ic[0][k], 1);
+            if (take) ic[2][k] += r;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q == 0 && give) continue;
+          const int fn = fam_of(q, b);
+          const size_t cell = (b >> 1 ? row1 : row0) + (q >> 1 ? col1 : col0);
+          float* nr = v.lam + (size_t)(LAM_NODE + 4 * fn) * ps + 4 * cell;
+          atomicAdd(reinterpret_cast<float4*>(nr),
+                    make_float4(nd[q][0], nd[q][1], nd[q][2], nd[q][3]));
+          if (a.variant == 0) {
+            float* ir = v.lam + (size_t)(LAM_INC + 4 * (4 * s + fn)) * ps + 4 * cell;
+            atomicAdd(reinterpret_cast<float4*>(ir),
+                      make_float4(ic[q][0], ic[q][1], ic[q][2], 0.f));
+          }
+        }
+      }
       if (!same) {
 #pragma unroll
         for (int b = 0; b < 3; ++b)
