@@ -84,6 +84,18 @@ __device__ __forceinline__ void node_d(const AdjView<T>& v, int s, int fam, size
 // [i0-1, i0+BX+2) x [j0-1, j0+BY+2), NPL planes; local plane lp < 16 is the
 // adjoint of lattice plane 4 fam + k (global LAM_NODE + lp), lp >= 16 the
 // adjoint of increment 12 s + 3 fam + k (global LAM_INC + lp - 16).
+// adds (a, b, c, d) to the 4-wide record at p (16-byte aligned), without
+// looking for zeros
+__device__ __forceinline__ void add4_always(float* p, float a, float b, float c, float d) {
+  atomicAdd(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+}
+__device__ __forceinline__ void add4_always(double* p, double a, double b, double c, double d) {
+  atomicAdd(p, a);
+  atomicAdd(p + 1, b);
+  atomicAdd(p + 2, c);
+  atomicAdd(p + 3, d);
+}
+
 // adds (a, b, c, d) to the 4-wide record at p (16-byte aligned)
 __device__ __forceinline__ void add4(float* p, float a, float b, float c, float d) {
   if (a != 0.f || b != 0.f || c != 0.f || d != 0.f)
@@ -431,28 +443,51 @@ __global__ void __launch_bounds__(256, 2) k_adj_points(const __grid_constant__ A
 // Acoustic increments (Sec. 6.1 step 1), reversed: Horner in r_s = c tau_s / h,
 // freezing c = sqrt(gamma p / rho), Z = rho c, and the transposed stencils.
 // ---------------------------------------------------------------------------
+// Wrapped neighbourhood of cell (ci, cj): columns ci-1, ci, ci+1 and row
+// offsets (cj-1) nx, cj nx, (cj+1) nx; a lattice offset resolves at compile
+// time to one of them.
+struct Nbhd {
+  int col[3];
+  size_t row[3];
+  __device__ __forceinline__ size_t at(int dc, int dr) const { return row[dr + 1] + col[dc + 1]; }
+};
+
+__device__ __forceinline__ Nbhd nbhd(int ci, int cj, int nx, int ny) {
+  Nbhd b;
+  b.col[1] = ci;
+  b.col[0] = ci == 0 ? nx - 1 : ci - 1;
+  b.col[2] = ci + 1 == nx ? 0 : ci + 1;
+  const int rm = cj == 0 ? ny - 1 : cj - 1, rp = cj + 1 == ny ? 0 : cj + 1;
+  b.row[0] = (size_t)rm * nx;
+  b.row[1] = (size_t)cj * nx;
+  b.row[2] = (size_t)rp * nx;
+  return b;
+}
+
 // node values (.p, .u, .v) at lattice offset (dx, dy) from the node of family
-// FAM of cell (ci, cj)
+// FAM of the neighbourhood's centre cell
 template <int FAM, typename T>
 struct LoadAdjPUV {
   const AdjView<T>* v;
-  int ci, cj;
+  Nbhd b;
   __device__ __forceinline__ PUV<T> operator()(int dx, int dy) const {
     const int ax = ((FAM == 2 || FAM == 3) ? 1 : 0) + dx, by = ((FAM == 1 || FAM == 3) ? 1 : 0) + dy;
-    const Prim<T> w = node_w(*v, fam_of(ax, by), cell_id(*v, ci + (ax >> 1), cj + (by >> 1)));
+    const Prim<T> w = node_w(*v, fam_of(ax, by), b.at(ax >> 1, by >> 1));
     PUV<T> o = {w.p, w.u, w.v};
     return o;
   }
 };
 
-// adds (lp, lu, lv) to the adjoint of the node at lattice offset (dx, dy)
-template <int FAM, typename T, typename Acc>
+// adds (lp, lu, lv) to the record of the node at lattice offset (dx, dy)
+template <int FAM, typename T>
 struct ScatterAdj {
-  Acc acc;
-  int ci, cj;
+  T* lam;
+  size_t ps;
+  Nbhd b;
   __device__ __forceinline__ void operator()(int dx, int dy, T lp, T lu, T lv) const {
     const int ax = ((FAM == 2 || FAM == 3) ? 1 : 0) + dx, by = ((FAM == 1 || FAM == 3) ? 1 : 0) + dy;
-    acc.node(fam_of(ax, by), ci + (ax >> 1), cj + (by >> 1), T(0), lu, lv, lp);
+    T* rec = lam + (size_t)(LAM_NODE + 4 * fam_of(ax, by)) * ps + 4 * b.at(ax >> 1, by >> 1);
+    add4_always(rec, T(0), lu, lv, lp);
   }
 };
 
@@ -478,7 +513,8 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
   const T dth = v.dt / v.h;
   const T r1 = c * dth;
   T Gp[3][4], Guv[3][4];
-  const LoadAdjPUV<FAM, T> ldr = {&v, i, j};
+  const Nbhd nb = nbhd(i, j, v.nx, v.ny);
+  const LoadAdjPUV<FAM, T> ldr = {&v, nb};
   sac_family<FAM, T>(ldr, wk.p, wk.u, wk.v, Gp, Guv);
   // polynomial coefficients c_o[q] (q = 1..4 stored at 0..3), as in increments_at
   T co[3][4];
@@ -526,7 +562,7 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
   const T lrho = c * lZ - lc * c / (T(2) * rk);
   const T lp = lc * c / (T(2) * pk);
   T lpK = T(0), luK = T(0), lvK = T(0);
-  const ScatterAdj<FAM, T, Acc> S = {acc, i, j};
+  const ScatterAdj<FAM, T> S = {v.lam, v.ps, nb};
   sac_family_adj<FAM, T>(S, lGp, lGuv, lpK, luK, lvK);
   acc.node(FAM, i, j, lrho, luK, lvK, lp + lpK);
 }
