@@ -650,13 +650,29 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
     const size_t idl = (size_t)gj * nx + im, idb = (size_t)jm * nx + gi,
                  idlb = (size_t)jm * nx + im;
     float lex[4], ley[4];  // adjoints of the x- and y-fluxes the point enters
+    if (fam == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float* lk = lin + (size_t)k * ps;
-      const float c = lk[id], l = lk[idl], b = lk[idb], lb = lk[idlb];
-      lex[k] = fam == 0 ? (c - l) + (b - lb) : c - l;
-      ley[k] = fam == 0 ? (c - b) + (l - lb) : c - b;
-      if (fam == 0) v.lam[(size_t)(LAM_OUT + k) * ps + id] = c;
+      for (int k = 0; k < 4; ++k) {
+        const float* lk = lin + (size_t)k * ps;
+        const float c = lk[id], l = lk[idl], b = lk[idb], lb = lk[idlb];
+        lex[k] = (c - l) + (b - lb);
+        ley[k] = (c - b) + (l - lb);
+        v.lam[(size_t)(LAM_OUT + k) * ps + id] = c;
+      }
+    } else if (fam == 1) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float* lk = lin + (size_t)k * ps;
+        lex[k] = lk[id] - lk[idl];
+        ley[k] = 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float* lk = lin + (size_t)k * ps;
+        lex[k] = 0.f;
+        ley[k] = lk[id] - lk[idb];
+      }
     }
     const int wcP = (py + 2) * CW + (px + 2);
     const float4 wp = W[fam * WPL + wcP];
