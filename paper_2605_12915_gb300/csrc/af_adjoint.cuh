@@ -745,24 +745,27 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
       if (a.variant == 0) {
         const float d2 = q2_eval<DCW>(Ds + 2 * DPL, Ds + 5 * DPL, Ds + 8 * DPL, Ds + 11 * DPL,
                                       dcf, lx, lyb);
-        const float rf = gas.rho_ref + rft, pf = gas.p_ref + pft, gp = gas.gamma * pf;
-        lwf[0] = ly[0] * (1.f + d2 / gp);
+        // (fast reciprocals, as the forward closure's division)
+        const float rf = gas.rho_ref + rft, pf = gas.p_ref + pft;
+        const float igp = __fdividef(1.f, gas.gamma * pf), ipf = __fdividef(1.f, pf);
+        lwf[0] = ly[0] * fmaf(d2, igp, 1.f);
         lwf[1] = ly[1];
         lwf[2] = ly[2];
-        lwf[3] = ly[3] - ly[0] * d2 * rf / (gp * pf);
+        lwf[3] = ly[3] - ly[0] * d2 * rf * igp * ipf;
         ld[0] = ly[1];
         ld[1] = ly[2];
-        ld[2] = ly[3] + ly[0] * rf / gp;
+        ld[2] = fmaf(ly[0] * rf, igp, ly[3]);
       } else {
         const int dcp = (py + 1) * DCW + (px + 1);
         const float d2 = Ds[(fam * 3 + 2) * DPL + dcp];
-        const float rp = gas.rho_ref + wp.x, pp = gas.p_ref + wp.w, gp = gas.gamma * pp;
+        const float rp = gas.rho_ref + wp.x, pp = gas.p_ref + wp.w;
+        const float igp = __fdividef(1.f, gas.gamma * pp), ipp = __fdividef(1.f, pp);
 #pragma unroll
         for (int k = 0; k < 4; ++k) lwf[k] = ly[k];
         // rho = rho_f + dp rho_P / (gamma p_P), with the increments at P itself
-        acc.inc(s, fam, gi, gj, ly[1], ly[2], ly[3] + ly[0] * rp / gp);
-        lrP += ly[0] * d2 / gp;
-        lpP += -ly[0] * d2 * rp / (gp * pp);
+        acc.inc(s, fam, gi, gj, ly[1], ly[2], fmaf(ly[0] * rp, igp, ly[3]));
+        lrP += ly[0] * d2 * igp;
+        lpP += -ly[0] * d2 * rp * igp * ipp;
         ld[0] = ld[1] = ld[2] = 0.f;
       }
       // adjoint of the foot's local coordinates.  D holds (u + du, v + dv, dp);
