@@ -41,6 +41,8 @@ struct AdjView {
   T h, dt;
   Gas<T> gas;
   int variant;
+  const double* lin64[16];  // lambda^{n+1} as given (FP64 device planes), read by
+                            // the fused reverse sweep in place of planes 0-15
 };
 
 constexpr int LAM_IN = 0, LAM_OUT = 16, LAM_NODE = 20, LAM_INC = 36, LAM_HALF = 68, LAM_FULL = 80;
@@ -634,7 +636,6 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
   const VecAdj<float> acc = vec_adj(v);
   const float th_full = a.dt / a.h;
   const float cst = a.dt / (36.f * a.h);
-  const float* lin = v.lam + (size_t)LAM_IN * ps;
   static_assert(TX == 32 && (3 * TX * TY) % NT == 0, "a warp is one row of one family");
   const int lane = threadIdx.x & 31;
   for (int t = threadIdx.x; t < 3 * TX * TY; t += NT) {
@@ -653,8 +654,9 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
     if (fam == 0) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float* lk = lin + (size_t)k * ps;
-        const float c = lk[id], l = lk[idl], b = lk[idb], lb = lk[idlb];
+        const double* lk = v.lin64[k];
+        const float c = (float)lk[id], l = (float)lk[idl], b = (float)lk[idb],
+                    lb = (float)lk[idlb];
         lex[k] = (c - l) + (b - lb);
         ley[k] = (c - b) + (l - lb);
         v.lam[(size_t)(LAM_OUT + k) * ps + id] = c;
@@ -662,16 +664,16 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
     } else if (fam == 1) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float* lk = lin + (size_t)k * ps;
-        lex[k] = lk[id] - lk[idl];
+        const double* lk = v.lin64[k];
+        lex[k] = (float)lk[id] - (float)lk[idl];
         ley[k] = 0.f;
       }
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float* lk = lin + (size_t)k * ps;
+        const double* lk = v.lin64[k];
         lex[k] = 0.f;
-        ley[k] = lk[id] - lk[idb];
+        ley[k] = (float)lk[id] - (float)lk[idb];
       }
     }
     const int wcP = (py + 2) * CW + (px + 2);
@@ -703,7 +705,7 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
       for (int k = 0; k < 4; ++k) {
         if (s == 0) o0[k] = o[k];
         else if (s == 1) lyh[k] = o[k];
-        else lyf[k] = o[k] + lin[(size_t)(4 + 4 * fam + k) * ps + id];
+        else lyf[k] = o[k] + (float)v.lin64[4 + 4 * fam + k][id];
       }
     }
     // ---- point update (Sec. 6.1 steps 3-4), reversed, both durations ----

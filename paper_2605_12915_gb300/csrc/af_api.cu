@@ -325,8 +325,8 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
     }
     cin.src[p] = src;
     cin.dst[p] = v.lam + (size_t)(LAM_IN + p) * v.ps;
+    v.lin64[p] = src;
   }
-  k_cast16<<<grid1d(h->N), 256, 0, s>>>(cin, h->N);
   dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
   // FP32 modes on grids the pipelined kernel accepts: one fused launch
   // recomputes each tile's step in shared memory and reverses its fluxes and
@@ -357,6 +357,8 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
       return af_sync(h);
     }
   }
+  // the stage-by-stage sweep reads lambda^{n+1} in the working precision
+  k_cast16<<<grid1d(h->N), 256, 0, s>>>(cin, h->N);
   // forward intermediates of the step from the handle's current state: the
   // pipelined fused kernel stores them where it runs (FP32 modes), else the
   // unfused kernels
