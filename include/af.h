@@ -99,7 +99,21 @@ enum {
  * are read on `where` (AF_HOST: pageable or pinned host memory; AF_DEVICE:
  * device memory of the current device); the caller keeps ownership.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
- * later call of this handle runs.  On error *out is NULL. */
+ * later call of this handle runs.  On error *out is NULL.
+ *
+ * The handle allocates two states and the step's scratch planes here (about
+ * 88 planes of nx * ny values of the working precision); af_adjoint_step
+ * allocates its own work area (92 planes) on its first call; af_destroy frees
+ * both.  Kernel choices, read from the environment when the handle is created
+ * (the results are the same up to rounding; they exist for comparison and
+ * testing): AF_PATH=ref runs the FP32 modes on the kernel-per-stage path
+ * instead of the fused kernel; AF_PIPE=0 replaces the persistent pipelined
+ * fused kernel by one CTA per tile, AF_PIPE=n caps its grid at n CTAs;
+ * AF_TMA=0 stages every tile by cp.async instead of tensor copies;
+ * AF_PREFETCH=0 disables the L2 prefetch of the one-CTA-per-tile kernel;
+ * AF_ZERO_COPY=0 copies pinned host planes through a staging buffer instead
+ * of converting them in place.  AF_ADJ_FUSED=0, read by each
+ * af_adjoint_step call, selects its stage-by-stage sweep. */
 af_status af_init(af_handle **out, const af_grid *g, double gamma, const af_state_f64 *state,
                   af_memory where, af_precision prec, af_variant var, void *cuda_stream);
 
@@ -135,8 +149,11 @@ af_status af_reduce_invariants(af_handle *h, double *out);
  * of the current state; both are FP64 arrays in the state layout above, on
  * `where`, owned by the caller (they may not overlap).  Adjoints are with
  * respect to the stored variables (cell averages and primitive point values).
- * The step's forward intermediates are recomputed in the handle's precision.
- * Synchronises the stream; returns the latched device error, if any. */
+ * The step's forward intermediates are recomputed in the handle's precision:
+ * in the FP32 modes on grids the pipelined fused kernel accepts, one launch
+ * recomputes each tile's step and reverses its fluxes and point updates in
+ * shared memory.  Synchronises the stream; returns the latched device error,
+ * if any. */
 af_status af_adjoint_step(af_handle *h, double dt, const af_state_f64 *lam_in,
                           const af_state_f64 *lam_out, af_memory where);
 
