@@ -91,11 +91,19 @@ def fused_kernel_name(nx, ny):
 
 
 def fused_source_hash():
+    """Hash of the fused kernel's code (comments, blank lines and indentation
+    removed, so that documentation edits keep a recorded profile valid)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in FUSED_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for line in text.splitlines():
+            line = line.split("//", 1)[0].strip()
+            if line:
+                h.update(line.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
