@@ -8,15 +8,23 @@
 //   D   acoustic increments (du, dv, dp) of every family for tau = dt/2 and
 //       tau = dt, cells [i0-1, i0+TX+3): every node of every cell that a
 //       convective foot can reach (phase 2).
-// Phase 3 evaluates the two-Picard foot and the transported (or additive)
-// point update of the points of cells [i0, i0+TX] x [j0, j0+TY] for both
-// durations; the half-step values never leave the SM.  Phase 4 forms the
-// space-time Simpson edge fluxes and updates the owned cell averages.
+// Phase 0 gathers the tile's input: in the one-tile-per-CTA kernels every
+// global load is issued at once (the averages wait in D until phase 1); in the
+// persistent kernel the raw planes of the next tile are copied into D while the
+// current tile finishes (2D tensor copies completing on an mbarrier, or 16-byte
+// cp.async on the periodic boundary), so phase 0 only waits for them and
+// converts them into W.  Phase 3 evaluates the two-Picard foot and the
+// transported (or additive) point update of the points of cells
+// [i0, i0+TX] x [j0, j0+TY] for both durations; the half-step values never
+// leave the SM.  Phase 4 forms the space-time Simpson edge fluxes and updates
+// the owned cell averages.  Two variants serve the adjoint: one also stores the
+// intermediates it linearises about (centres, increments, half-step points),
+// the other stops after phase 3 with D still in shared memory, for the reverse
+// sweep of the same tile.
 //
 // Planes of one family are rows of consecutive cells, so a warp working on 32
 // consecutive cells touches consecutive addresses: no bank conflicts, and
-// stencil offsets become load immediates.  Phase 0 issues every global load of
-// the step at once (the averages wait in the increment region until phase 1).  A convective foot may lie up to one
+// stencil offsets become load immediates.  A convective foot may lie up to one
 // cell from its point in each direction; displacements are clamped there and
 // flagged, so every shared-memory access stays in bounds whatever the data.
 #pragma once
