@@ -243,6 +243,39 @@ def random_smooth(nx, ny, seed=0, amp=0.05, n_modes=4, flow=(0.3, -0.2), cfl=0.4
     return Problem("random", g, gamma, st, dt_from_cfl(st, g, cfl, gamma), 0)
 
 
+def smooth_direction(grid, seed, n_modes=3):
+    """Seeded smooth direction in state space, scaled to max |d| = 1: for each of
+    the four components k a sum of n_modes periodic Fourier modes phi_k (wave
+    numbers in [-3, 3] per axis), sampled at the cell centres (planes k) and at
+    the vertex, x-edge and y-edge nodes (planes 4 + k, 8 + k, 12 + k).  Used as
+    a perturbation or a finite-difference direction; being smooth across the
+    node families, it does not excite grid-scale modes."""
+    rng = np.random.default_rng(seed)
+    nx, ny, h = grid.nx, grid.ny, grid.h
+    Lx, Ly = nx * h, ny * h
+    terms = [[(int(rng.integers(-3, 4)), int(rng.integers(-3, 4)), rng.uniform(-1.0, 1.0),
+               rng.uniform(0.0, 2 * np.pi)) for _ in range(n_modes)] for _ in range(4)]
+
+    def sample(k, ox, oy):
+        x = (grid.x0 + h * (np.arange(nx) + ox)) / Lx
+        y = (grid.y0 + h * (np.arange(ny) + oy)) / Ly
+        out = np.zeros((ny, nx))
+        for mx, my, a, ph in terms[k]:
+            # separable: cos(A + B) = Re(e^{iA} e^{iB})
+            out += a * np.real(np.exp(2j * np.pi * my * y + 1j * ph)[:, None] *
+                               np.exp(2j * np.pi * mx * x)[None, :])
+        return out
+
+    d = np.empty((16, ny, nx))
+    for k in range(4):
+        d[k] = sample(k, 0.5, 0.5)
+    for base, (ox, oy) in ((4, (0.0, 0.0)), (8, (0.0, 0.5)), (12, (0.5, 0.0))):
+        for k in range(4):
+            d[base + k] = sample(k, ox, oy)
+    m = np.max(np.abs(d))
+    return d / m if m > 0 else d
+
+
 def uniform(nx, ny, rho=1.0, u=0.3, v=-0.7, p=0.9, cfl=0.4, gamma=GAMMA, h=0.1):
     g = Grid(nx, ny, 0.0, 0.0, h)
     st = build_state(g, lambda x, y: (rho + 0 * x, u + 0 * x, v + 0 * x, p + 0 * x), gamma)
