@@ -94,6 +94,81 @@ def test_pulse_512_fp32_vs_fp64_100_steps(precision):
     assert err < TOL32
 
 
+def _mirror_x(st):
+    """Reflection x -> -x on the symmetric grid [-L, L] with an even cell count."""
+    out = np.empty_like(st)
+    cell = lambda a: a[:, ::-1]
+    vert = lambda a: np.roll(a[:, ::-1], 1, axis=1)
+    for k in range(4):
+        sgn = -1.0 if k == 1 else 1.0
+        out[k] = sgn * cell(st[k])
+        out[4 + k] = sgn * vert(st[4 + k])
+        out[8 + k] = sgn * vert(st[8 + k])
+        out[12 + k] = sgn * cell(st[12 + k])
+    return out
+
+
+def _swap_xy(st):
+    """Reflection x <-> y: E_v and E_h exchange, u and v exchange."""
+    out = np.empty_like(st)
+    perm = [0, 2, 1, 3]
+    for k in range(4):
+        out[perm[k]] = st[k].T
+        out[4 + perm[k]] = st[4 + k].T
+        out[8 + perm[k]] = st[12 + k].T
+        out[12 + perm[k]] = st[8 + k].T
+    return out
+
+
+def _pressure_at(st, wc, X, Y):
+    """Q2 reconstruction of p at points (X, Y) in cell units (vectorised; the
+    centre values wc come from the oracle's centre recovery)."""
+    ny, nx = st.shape[1:]
+    ci, cj = np.floor(X).astype(int), np.floor(Y).astype(int)
+    L = lambda s: (0.5 * s * (s - 1), 1 - s * s, 0.5 * s * (s + 1))
+    lx, ly = L(2 * (X - ci) - 1), L(2 * (Y - cj) - 1)
+    i0, i1, j0, j1 = ci % nx, (ci + 1) % nx, cj % ny, (cj + 1) % ny
+    V, Ev, Eh, C = st[7], st[11], st[15], wc[3]
+    rows = [(V[j0, i0], Eh[j0, i0], V[j0, i1]), (Ev[j0, i0], C[j0, i0], Ev[j0, i1]),
+            (V[j1, i0], Eh[j1, i0], V[j1, i1])]
+    return sum(ly[b] * sum(lx[a] * rows[b][a] for a in range(3)) for b in range(3))
+
+
+def _radial_error(orc, P, st):
+    """max over radii r in [0.1, 0.9] of (max - min) of p over 256 angles."""
+    wc, fl = orc.center_recovery(st, P.gamma)
+    assert fl == 0
+    th = np.linspace(0.0, 2 * np.pi, 256, endpoint=False)
+    worst = 0.0
+    for r in np.linspace(0.1, 0.9, 33):
+        X = (r * np.cos(th) - P.grid.x0) / P.grid.h
+        Y = (r * np.sin(th) - P.grid.y0) / P.grid.h
+        p = _pressure_at(st, wc, X, Y)
+        worst = max(worst, float(p.max() - p.min()))
+    return worst
+
+
+def test_pulse_512_400_steps_symmetry_and_fp32(orc):
+    """The Gaussian pulse workload in full (512^2, 400 steps): the FP64 state keeps
+    the grid's mirror and diagonal symmetry to rounding (measured 1e-14), its
+    radial-symmetry error stays small (measured 6.9e-6 of the pulse's pressure
+    amplitude), and both FP32 modes stay within 2e-5 of FP64 (measured 3.5e-6)."""
+    P = I.pulse(n=512)
+    amp = float(np.max(P.state[7]) - np.min(P.state[7]))
+    b = run_gpu(P, 400, "fp64")
+    scale = np.max(np.abs(b))
+    assert np.max(np.abs(_mirror_x(b) - b)) / scale < 1e-13
+    assert np.max(np.abs(_swap_xy(b) - b)) / scale < 1e-13
+    rad = _radial_error(orc, P, b) / amp
+    print("pulse 512^2, 400 steps: radial-symmetry error / amplitude", rad)
+    assert rad < 1e-4
+    for precision in ("fp32", "fp32_comp"):
+        a = run_gpu(P, 400, precision)
+        err = rel_linf(a, b)
+        print("pulse 512^2, 400 steps,", precision, "vs fp64 rel Linf", err)
+        assert err < TOL32
+
+
 def test_free_stream(orc):
     P = I.uniform(33, 17)
     for prec, tol in (("fp64", 1e-14), ("fp32", 1e-6), ("fp32_comp", 1e-6)):
