@@ -103,8 +103,10 @@ enum {
  *
  * The handle allocates two states and the step's scratch planes here (about
  * 88 planes of nx * ny values of the working precision); af_adjoint_step
- * allocates its own work area (92 planes) on its first call; af_destroy frees
- * both.  Kernel choices, read from the environment when the handle is created
+ * allocates its own work area (92 planes) on its first call, host transfers
+ * of pageable planes a staging buffer of 16 FP64 planes on their first use,
+ * af_exchange_state another 16 FP64 planes and a second stream with host
+ * planes; af_destroy frees all of them.  Kernel choices, read from the environment when the handle is created
  * (the results are the same up to rounding; they exist for comparison and
  * testing): AF_PATH=ref runs the FP32 modes on the kernel-per-stage path
  * instead of the fused kernel; AF_PIPE=0 replaces the persistent pipelined
@@ -137,6 +139,26 @@ af_status af_get_state(af_handle *h, const af_state_f64 *out, af_memory where);
  * latched device error.  AF_HOST planes in pinned memory are read directly by
  * the conversion kernel, pageable ones are copied first. */
 af_status af_set_state(af_handle *h, const af_state_f64 *in, af_memory where);
+
+/* Hands the current state out into `out` and takes `in` in as the new current
+ * state (as af_get_state then af_set_state), for callers that stream states
+ * through the handle: set, step, then exchange the result for the next input.
+ * `out` and `in` are FP64 planes on `where`, owned by the caller, and may not
+ * share a byte (AF_ERR_ARG).  The call returns once the new state is in place
+ * (the latched device error cleared).
+ * AF_DEVICE: `out` is complete on return too.
+ * AF_HOST: both transfers run on copy engines on two streams of the handle, so
+ * that they overlap on the host-device link with each other and with a step
+ * still running: `in` is copied into a device staging buffer at once, the
+ * outgoing state is converted into a second one (16 FP64 planes each,
+ * allocated on first use, held until af_destroy) and copied into `out`.  That
+ * last copy may still be in flight on return; later calls of this handle that
+ * touch it are ordered after it (af_step does not wait for it, so the next
+ * step overlaps it), but the caller itself may read or write `out` only once
+ * af_sync, or any other call of this handle but af_step and
+ * af_exchange_state, has returned.  `in` is read before the call returns. */
+af_status af_exchange_state(af_handle *h, const af_state_f64 *out, const af_state_f64 *in,
+                            af_memory where);
 
 /* FP64 global diagnostics of the current state, out[AF_NINV] in host memory.
  * Synchronises the stream. */

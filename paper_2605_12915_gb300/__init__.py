@@ -69,6 +69,9 @@ def load():
         lib.af_get_state.restype = ctypes.c_int
         lib.af_set_state.argtypes = [vp, ctypes.POINTER(AfState), ctypes.c_int]
         lib.af_set_state.restype = ctypes.c_int
+        lib.af_exchange_state.argtypes = [vp, ctypes.POINTER(AfState), ctypes.POINTER(AfState),
+                                          ctypes.c_int]
+        lib.af_exchange_state.restype = ctypes.c_int
         lib.af_reduce_invariants.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.af_reduce_invariants.restype = ctypes.c_int
         lib.af_adjoint_step.argtypes = [vp, d, ctypes.POINTER(AfState), ctypes.POINTER(AfState),
@@ -168,6 +171,18 @@ def af_set_state(handle, state):
                                AF_DEVICE if dev else AF_HOST)
 
 
+def af_exchange_state(handle, out, state):
+    """out <- the current state, then the current state <- state (both host or
+    both device arrays of shape (16, ny, nx), float64)."""
+    pout, dout = _array_ptr(out)
+    pin, din = _array_ptr(state)
+    assert dout == din, "out and state must both be host or both be device arrays"
+    n = state.shape[1] * state.shape[2]
+    so, si = _state_struct(pout, n), _state_struct(pin, n)
+    return load().af_exchange_state(ctypes.c_void_p(handle), ctypes.byref(so), ctypes.byref(si),
+                                     AF_DEVICE if din else AF_HOST)
+
+
 def af_reduce_invariants(handle, out):
     """out: float64 numpy array of AF_NINV values (host)."""
     import numpy as np
@@ -230,6 +245,14 @@ class Solver:
         rc = af_set_state(self.handle, state)
         if rc != AF_OK:
             raise AfError(rc, "af_set_state")
+
+    def exchange(self, out, state):
+        """Hand the current state out into `out` and take `state` in (see
+        af_exchange_state); returns out."""
+        rc = af_exchange_state(self.handle, out, state)
+        if rc != AF_OK:
+            raise AfError(rc, "af_exchange_state")
+        return out
 
     def invariants(self):
         import numpy as np

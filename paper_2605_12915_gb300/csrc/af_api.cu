@@ -49,6 +49,12 @@ struct af_handle {
   int tma;               // 1: the pipelined kernel stages interior tiles by tensor copies
   int zero_copy;         // 1: pinned host planes are converted in place (AF_ZERO_COPY=0: copies)
   void* adj_arena;       // adjoint arena (lazy): LAM_PLANES planes, see AdjView
+  double* xstaging;      // 16 FP64 planes of af_exchange_state's outgoing state (lazy)
+  cudaStream_t aux;      // af_exchange_state: outgoing copies (lazy)
+  cudaStream_t aux_in;   // af_exchange_state: incoming copies (lazy)
+  cudaEvent_t ev_fork, ev_join, ev_in;
+  int out_pending;       // 1: the outgoing copies of the last exchange may be in flight
+  af_state_f64 pending_out;  // ... into these planes
 };
 
 namespace {
@@ -253,7 +259,9 @@ const void* mapped_host_plane(const af_handle* h, const void* p) {
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
-af_status import_state(af_handle* h, const af_state_f64* in, af_memory where) {
+// Enqueues the conversion of `in` into the current state on the handle's
+// stream (pageable host planes are first copied to the staging buffer).
+af_status import_enqueue(af_handle* h, const af_state_f64* in, af_memory where) {
   F64Planes src;
   if (where == AF_HOST) {
     // pinned planes are read in place by the import kernel, pageable ones are
@@ -277,11 +285,54 @@ af_status import_state(af_handle* h, const af_state_f64* in, af_memory where) {
     case AF_FP32: k_import<float, false><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N, offsets_of(h)); break;
     case AF_FP32_COMP: k_import<float, true><<<g, 256, 0, h->stream>>>(src, planes_of<float>(h, h->cur), h->N, offsets_of(h)); break;
   }
+  if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+  return AF_OK;
+}
+
+// Orders the handle's stream after the outgoing copies of the last
+// af_exchange_state, which may still be in flight on the aux stream.
+af_status wait_outgoing(af_handle* h) {
+  if (h->out_pending && cudaStreamWaitEvent(h->stream, h->ev_join, 0) != cudaSuccess)
+    return cuda_fail(h);
+  return AF_OK;
+}
+
+// Clears the latched device error once the stream has passed the new state
+// (and, the caller having called wait_outgoing, any outgoing copies).
+af_status import_finish(af_handle* h) {
   if (cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned), h->stream) != cudaSuccess) return cuda_fail(h);
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
   *(volatile unsigned*)h->h_flags = 0;
+  h->out_pending = 0;
   return AF_OK;
+}
+
+af_status import_state(af_handle* h, const af_state_f64* in, af_memory where) {
+  af_status st = import_enqueue(h, in, where);
+  return st != AF_OK ? st : import_finish(h);
+}
+
+// Enqueues the conversion of the current state into the FP64 planes dst.
+af_status export_enqueue(af_handle* h, const F64Out& dst) {
+  int g = grid1d(h->N);
+  switch (h->prec) {
+    case AF_FP64: k_export<double, false><<<g, 256, 0, h->stream>>>(planes_of<double>(h, h->cur), dst, h->N, offsets_of(h)); break;
+    case AF_FP32: k_export<float, false><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N, offsets_of(h)); break;
+    case AF_FP32_COMP: k_export<float, true><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N, offsets_of(h)); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? AF_OK : cuda_fail(h);
+}
+
+// true when some plane of a and some plane of b share a byte
+bool planes_overlap(const af_state_f64* a, const af_state_f64* b, size_t bytes) {
+  for (int p = 0; p < 16; ++p)
+    for (int q = 0; q < 16; ++q) {
+      const char* x = (const char*)plane_in(a, p);
+      const char* y = (const char*)plane_in(b, q);
+      if (x < y + bytes && y < x + bytes) return true;
+    }
+  return false;
 }
 
 }  // namespace
@@ -562,10 +613,12 @@ af_status af_sync(af_handle* h) {
   if (!h) return AF_ERR_ARG;
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
+  if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
   if (cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
                       h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return cuda_fail(h);
+  h->out_pending = 0;
   return map_flags(*(volatile unsigned*)h->h_flags);
 }
 
@@ -574,6 +627,7 @@ af_status af_set_state(af_handle* h, const af_state_f64* in, af_memory where) {
     return AF_ERR_ARG;
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
+  if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
   return import_state(h, in, where);
 }
 
@@ -582,6 +636,7 @@ af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
     return AF_ERR_ARG;
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
+  if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
   F64Out dst;
   bool copy_back[16] = {};
   if (where == AF_HOST) {
@@ -598,13 +653,8 @@ af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
   } else {
     for (int p = 0; p < 16; ++p) dst.p[p] = (double*)plane_in(out, p);
   }
-  int g = grid1d(h->N);
-  switch (h->prec) {
-    case AF_FP64: k_export<double, false><<<g, 256, 0, h->stream>>>(planes_of<double>(h, h->cur), dst, h->N, offsets_of(h)); break;
-    case AF_FP32: k_export<float, false><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N, offsets_of(h)); break;
-    case AF_FP32_COMP: k_export<float, true><<<g, 256, 0, h->stream>>>(planes_of<float>(h, h->cur), dst, h->N, offsets_of(h)); break;
-  }
-  if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
+  af_status est = export_enqueue(h, dst);
+  if (est != AF_OK) return est;
   for (int p = 0; p < 16; ++p)
     if (copy_back[p] &&
         cudaMemcpyAsync((void*)plane_in(out, p), dst.p[p], sizeof(double) * h->N,
@@ -613,10 +663,88 @@ af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
   return af_sync(h);
 }
 
+af_status af_exchange_state(af_handle* h, const af_state_f64* out, const af_state_f64* in,
+                            af_memory where) {
+  if (!h || check_state_ptrs(out) != AF_OK || check_state_ptrs(in) != AF_OK ||
+      (where != AF_HOST && where != AF_DEVICE))
+    return AF_ERR_ARG;
+  if (planes_overlap(out, in, sizeof(double) * h->N)) return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  DeviceGuard guard(h->device);
+  if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
+  if (where == AF_DEVICE) {
+    F64Out dst;
+    for (int p = 0; p < 16; ++p) dst.p[p] = (double*)plane_in(out, p);
+    af_status st = export_enqueue(h, dst);
+    if (st == AF_OK) st = import_enqueue(h, in, AF_DEVICE);
+    return st != AF_OK ? st : import_finish(h);
+  }
+  // host: both directions by copy engines, on two streams of their own, so that
+  // they overlap on the link with each other and with the step still running:
+  //   aux_in  in -> staging (FP64)                       (starts at once)
+  //   stream  [earlier work] state -> xstaging (export), then, once aux_in is
+  //           done, staging -> state (import)
+  //   aux     xstaging -> out, after the export; left in flight on return
+  if (!h->xstaging && cudaMalloc(&h->xstaging, sizeof(double) * 16 * h->N) != cudaSuccess) {
+    h->xstaging = nullptr;
+    return AF_ERR_ALLOC;
+  }
+  af_status st = ensure_staging(h);
+  if (st != AF_OK) return st;
+  if (!h->aux) {
+    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->aux_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(h);
+  }
+  // an incoming plane that is also the target of the last exchange's outgoing
+  // copies is read after them
+  if (h->out_pending && planes_overlap(&h->pending_out, in, sizeof(double) * h->N) &&
+      cudaStreamWaitEvent(h->aux_in, h->ev_join, 0) != cudaSuccess)
+    return cuda_fail(h);
+  // the staging buffer is idle: every earlier call that used it has synchronised
+  af_state_f64 staged;
+  for (int k = 0; k < 4; ++k) {
+    staged.avg[k] = h->staging + (size_t)k * h->N;
+    staged.vtx[k] = h->staging + (size_t)(4 + k) * h->N;
+    staged.ev[k] = h->staging + (size_t)(8 + k) * h->N;
+    staged.eh[k] = h->staging + (size_t)(12 + k) * h->N;
+  }
+  for (int p = 0; p < 16; ++p)
+    if (cudaMemcpyAsync((void*)plane_in(&staged, p), plane_in(in, p), sizeof(double) * h->N,
+                        cudaMemcpyHostToDevice, h->aux_in) != cudaSuccess)
+      return cuda_fail(h);
+  if (cudaEventRecord(h->ev_in, h->aux_in) != cudaSuccess) return cuda_fail(h);
+  F64Out dst;
+  for (int p = 0; p < 16; ++p) dst.p[p] = h->xstaging + (size_t)p * h->N;
+  st = export_enqueue(h, dst);
+  if (st != AF_OK) return st;
+  if (cudaEventRecord(h->ev_fork, h->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(h->aux, h->ev_fork, 0) != cudaSuccess)
+    return cuda_fail(h);
+  for (int p = 0; p < 16; ++p)
+    if (cudaMemcpyAsync((void*)plane_in(out, p), dst.p[p], sizeof(double) * h->N,
+                        cudaMemcpyDeviceToHost, h->aux) != cudaSuccess)
+      return cuda_fail(h);
+  if (cudaEventRecord(h->ev_join, h->aux) != cudaSuccess ||
+      cudaStreamWaitEvent(h->stream, h->ev_in, 0) != cudaSuccess)
+    return cuda_fail(h);
+  st = import_enqueue(h, &staged, AF_DEVICE);
+  if (st == AF_OK) st = import_finish(h);
+  if (st == AF_OK) {
+    h->out_pending = 1;
+    h->pending_out = *out;
+  }
+  return st;
+}
+
 af_status af_reduce_invariants(af_handle* h, double* out) {
   if (!h || !out) return AF_ERR_ARG;
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
+  if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
   double* partial = h->d_red;
   double* res = h->d_red + (size_t)RED_VALS * h->red_blocks;
   dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
@@ -663,6 +791,7 @@ af_status af_adjoint_step(af_handle* h, double dt, const af_state_f64* lam_in,
     return AF_ERR_ARG;
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
+  if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
   switch (h->prec) {
     case AF_FP64: return adjoint_impl<double, false>(h, dt, lam_in, lam_out, where);
     case AF_FP32: return adjoint_impl<float, false>(h, dt, lam_in, lam_out, where);
@@ -681,6 +810,16 @@ void af_destroy(af_handle* h) {
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->d_red) cudaFree(h->d_red);
   if (h->adj_arena) cudaFree(h->adj_arena);
+  if (h->xstaging) cudaFree(h->xstaging);
+  if (h->aux) {
+    cudaStreamSynchronize(h->aux);
+    cudaStreamSynchronize(h->aux_in);
+    cudaStreamDestroy(h->aux);
+    cudaStreamDestroy(h->aux_in);
+    cudaEventDestroy(h->ev_fork);
+    cudaEventDestroy(h->ev_join);
+    cudaEventDestroy(h->ev_in);
+  }
   if (h->h_red) cudaFreeHost(h->h_red);
   delete[] h->tmaps;
   delete h;

@@ -88,6 +88,9 @@ def test_calls_on_a_null_handle_are_refused(libaf):
     assert libaf.af_step(None, ctypes.c_double(0.1), 1) == AF_ERR_ARG
     libaf.af_sync.argtypes = [ctypes.c_void_p]
     assert libaf.af_sync(None) == AF_ERR_ARG
+    libaf.af_exchange_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int]
+    assert libaf.af_exchange_state(None, None, None, 0) == AF_ERR_ARG
     libaf.af_destroy.argtypes = [ctypes.c_void_p]
     libaf.af_destroy(None)  # a no-op
 

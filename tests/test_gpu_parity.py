@@ -412,3 +412,70 @@ def test_full_size_shear_2048_windows_match_oracle(orc):
         worst = max(worst, float(np.max(err)))
     print("2048^2 window parity, FP32 vs FP64 oracle, rel Linf", worst)
     assert worst < TOL32
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_comp"])
+def test_exchange_is_get_then_set(precision):
+    """af_exchange_state = af_get_state then af_set_state, bitwise, for pinned
+    and pageable host planes and device planes; overlapping planes are refused."""
+    import torch
+    P = I.random_smooth(70, 44, seed=41, amp=0.05)
+    Q = I.random_smooth(70, 44, seed=42, amp=0.05)
+    ref = af.Solver(P.grid, P.gamma, P.state, precision=precision)
+    ref.step(P.dt, 3)
+    want_out = ref.state()
+    ref.set_state(Q.state)
+    ref.step(Q.dt, 2)
+    want_next = ref.state()
+    ref.close()
+    pinned_in = torch.from_numpy(Q.state.copy()).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    cases = [("pinned", pinned_out, pinned_in),
+             ("pageable", np.empty_like(Q.state), Q.state.copy()),
+             ("device", torch.empty(Q.state.shape, dtype=torch.float64, device="cuda"),
+              torch.from_numpy(Q.state.copy()).cuda())]
+    for name, out, new in cases:
+        s = af.Solver(P.grid, P.gamma, P.state, precision=precision)
+        s.step(P.dt, 3)
+        s.exchange(out, new)
+        s.step(Q.dt, 2)
+        s.sync()  # host `out` may still be arriving until a call other than step
+        got = out.cpu().numpy() if hasattr(out, "cpu") else out
+        assert np.array_equal(got, want_out), name
+        assert np.array_equal(s.state(), want_next), name
+        with pytest.raises(af.AfError):
+            s.exchange(new, new)
+        s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_comp"])
+def test_exchange_chain_through_pinned_buffers(precision):
+    """Streaming through host buffers: the state handed out by one exchange is
+    taken back in by the next (whose incoming copy must wait for that outgoing
+    one), while the same output buffer is reused."""
+    import torch
+    P = I.random_smooth(64, 40, seed=43, amp=0.05)
+    Q = I.random_smooth(64, 40, seed=44, amp=0.05)
+    ref = af.Solver(P.grid, P.gamma, P.state, precision=precision)
+    ref.set_state(Q.state)
+    q_round = ref.state()  # Q through the working precision
+    ref.set_state(P.state)
+    ref.step(P.dt, 1)
+    s1 = ref.state()
+    ref.step(P.dt, 1)
+    s2 = ref.state()
+    ref.close()
+    A = torch.empty(P.state.shape, dtype=torch.float64).pin_memory()
+    B = torch.from_numpy(Q.state.copy()).pin_memory()
+    C = torch.empty_like(A).pin_memory()
+    s = af.Solver(P.grid, P.gamma, P.state, precision=precision)
+    s.step(P.dt, 1)
+    s.exchange(A, B)  # A <- S1 (in flight), state <- Q
+    s.exchange(C, A)  # C <- Q, state <- A = S1 once it has arrived
+    s.step(P.dt, 1)
+    s.exchange(C, B)  # C <- S2, reused while the previous copy into it may be in flight
+    s.sync()
+    assert np.array_equal(A.numpy(), s1)
+    assert np.array_equal(C.numpy(), s2)
+    assert np.array_equal(s.state(), q_round)
+    s.close()
