@@ -413,7 +413,9 @@ def ensemble_block(af, I, stream, torch, n_problems=256, steps=200):
         s.close()
     return {"problems": n_problems, "cells": cells, "steps": steps,
             "batched": {"value": cells * steps / (ms_batch * 1e-3), "unit": UNIT, "ms": ms_batch,
-                        "tile_geometry": ["32x32/512", "24x16/256x2", "16x16/256x3"][geom],
+                        "tile_geometry": ["32x32/512 per tile", "24x16/256x2 per tile",
+                                          "16x16/256x3 per tile",
+                                          "32x32/512 persistent, staged"][geom],
                         "tune_ms_per_step": tune},
             "sequential": {"value": cells * steps / (ms_seq * 1e-3), "unit": UNIT, "ms": ms_seq},
             "speedup": ms_seq / ms_batch}

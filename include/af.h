@@ -211,9 +211,17 @@ af_status af_step_noalloc(const af_grid *g, double gamma, double dt, af_variant 
  * state) advanced together: every step is one launch of the fused FP32 kernel
  * over a table of the tiles of all grids, and the launches of an af_batch_step
  * call are captured once in a CUDA graph (re-captured when n_steps changes).
- * The first af_batch_step times the compiled tile geometries on the actual
+ * Geometries (AF_BATCH_GEOMS): 0, 1, 2 launch one CTA per tile of 32x32,
+ * 24x16 or 16x16 cells; 3 launches persistent CTAs (one per SM) that step
+ * through the 32x32 tiles of all grids, staging each next tile (tensor copies
+ * inside a grid, cp.async on its periodic boundary) while the current one
+ * finishes -- offered when every grid has nx a multiple of 4, nx >= 40 and
+ * ny >= 38.  The first af_batch_step times the geometries on the actual
  * ensemble (states are snapshotted and restored around the trials) and keeps
- * the fastest.  Per-grid results are bitwise those of af_step on a lone handle. */
+ * the fastest; AF_BATCH_GEOM=g in the environment of af_batch_init fixes
+ * geometry g instead (for comparison and testing).  Per-grid results are
+ * bitwise those of af_step on a lone handle. */
+#define AF_BATCH_GEOMS 4
 typedef struct af_batch af_batch;
 
 /* n grids; grids[k], states[k] as in af_init; prec must be AF_FP32 or
@@ -234,8 +242,9 @@ af_status af_batch_sync(af_batch *b);
 /* State of grid k (as af_get_state). */
 af_status af_batch_get_state(af_batch *b, int32_t k, const af_state_f64 *out, af_memory where);
 
-/* The tile geometry chosen by the autotuner (index, -1 before the first step)
- * and, if tune_ms is not NULL, the per-step time of each candidate (3 floats). */
+/* The tile geometry in use (index, -1 before the first step) and, if tune_ms is
+ * not NULL, the per-step time of each candidate as timed by the autotuner
+ * (AF_BATCH_GEOMS floats; -1 for a geometry not timed). */
 af_status af_batch_info(af_batch *b, int32_t *geometry, float *tune_ms);
 
 void af_batch_destroy(af_batch *b);

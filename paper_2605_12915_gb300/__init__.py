@@ -21,6 +21,7 @@ AF_FP64, AF_FP32, AF_FP32_COMP = 0, 1, 2
 AF_TAI, AF_RB = 0, 1
 AF_HOST, AF_DEVICE = 0, 1
 AF_NINV = 12
+AF_BATCH_GEOMS = 4
 INVARIANT_NAMES = ["mass", "mom_x", "mom_y", "energy", "entropy_simpson", "entropy_avg",
                    "kinetic_energy", "max_wave_speed", "min_rho", "min_p",
                    "vorticity_integral", "flags"]
@@ -336,7 +337,7 @@ class Batch:
 
     def info(self):
         g = ctypes.c_int32()
-        t = (ctypes.c_float * 3)()
+        t = (ctypes.c_float * AF_BATCH_GEOMS)()
         load().af_batch_info(ctypes.c_void_p(self.handle), ctypes.byref(g), t)
         return g.value, list(t)
 

@@ -847,16 +847,21 @@ struct af_batch {
   int graph_steps, graph_parity;
   void* snapshot;           // device copy of every state while tuning
   int own_stream;           // the batch created its stream (the legacy stream cannot be captured)
+  int pipe_ok;              // every grid meets the persistent kernel's staging conditions
+  int pipe_ctas;            // its CTAs
+  TileMaps* d_maps[2];      // device, one per grid and parity (null: cp.async staging only)
 };
 
 namespace {
 
 af_status batch_launch(af_batch* b, int geom, int parity) {
   const StepArgs<float>* args = b->d_args + (size_t)parity * b->n;
+  if (BATCH_GEOMS[geom].pipe && !b->pipe_ok) return AF_ERR_ARG;
   cudaError_t e = b->prec == AF_FP32_COMP
-                      ? launch_batch<true>(geom, b->stream, args, b->d_tiles[geom], b->ntiles[geom])
+                      ? launch_batch<true>(geom, b->stream, args, b->d_tiles[geom], b->ntiles[geom],
+                                           b->d_maps[parity], b->pipe_ctas)
                       : launch_batch<false>(geom, b->stream, args, b->d_tiles[geom],
-                                            b->ntiles[geom]);
+                                            b->ntiles[geom], b->d_maps[parity], b->pipe_ctas);
   return e == cudaSuccess ? AF_OK : AF_ERR_CUDA;
 }
 
@@ -898,6 +903,8 @@ af_status batch_tune(af_batch* b) {
   cudaEventCreate(&e1);
   float best = 1e30f;
   for (int g = 0; g < N_BATCH_GEOMS && st == AF_OK; ++g) {
+    b->tune_ms[g] = -1.f;
+    if (BATCH_GEOMS[g].pipe && !b->pipe_ok) continue;
     int parity = batch_parity(b);
     st = batch_launch(b, g, parity);  // warm-up, attribute set-up
     parity ^= 1;
@@ -994,6 +1001,43 @@ af_status af_batch_init(af_batch** out, int32_t n, const af_grid* grids, double 
     af_batch_destroy(b);
     return AF_ERR_ALLOC;
   }
+  // the persistent pipelined geometry: every grid must allow its staging; the
+  // handles' tensor maps (encoded by af_init) go to the device when all have them
+  b->pipe_ctas = b->h[0]->pipe_ctas;
+  b->pipe_ok = b->pipe_ctas > 0;
+  bool tma = true;
+  for (int k = 0; k < n && b->pipe_ok; ++k) {
+    af_handle* h = b->h[k];
+    for (int p = 0; p < 2; ++p) {
+      const int cur = h->cur;
+      h->cur = p;
+      const StepArgs<float> a = step_args<float>(h, 1.0);
+      h->cur = cur;
+      if (!pipe_eligible(a)) b->pipe_ok = 0;
+    }
+    tma = tma && h->tma;
+  }
+  if (b->pipe_ok && tma) {
+    for (int p = 0; p < 2 && ok; ++p) {
+      ok = cudaMalloc(&b->d_maps[p], sizeof(TileMaps) * n) == cudaSuccess;
+      for (int k = 0; k < n && ok; ++k)
+        ok = cudaMemcpy(&b->d_maps[p][k], &b->h[k]->tmaps[p], sizeof(TileMaps),
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
+      af_batch_destroy(b);
+      return AF_ERR_ALLOC;
+    }
+  }
+  // AF_BATCH_GEOM=g fixes the geometry instead of timing the candidates
+  const char* fg = getenv("AF_BATCH_GEOM");
+  if (fg && fg[0] >= '0' && fg[0] < '0' + N_BATCH_GEOMS && !fg[1]) {
+    const int g = fg[0] - '0';
+    if (!BATCH_GEOMS[g].pipe || b->pipe_ok) {
+      b->geom = g;
+      for (int q = 0; q < N_BATCH_GEOMS; ++q) b->tune_ms[q] = -1.f;
+    }
+  }
   *out = b;
   return AF_OK;
 }
@@ -1089,6 +1133,8 @@ void af_batch_destroy(af_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (int g = 0; g < N_BATCH_GEOMS; ++g)
     if (b->d_tiles[g]) cudaFree(b->d_tiles[g]);
+  for (int p = 0; p < 2; ++p)
+    if (b->d_maps[p]) cudaFree(b->d_maps[p]);
   if (b->d_args) cudaFree(b->d_args);
   if (b->h_args) cudaFreeHost(b->h_args);
   if (b->snapshot) cudaFree(b->snapshot);

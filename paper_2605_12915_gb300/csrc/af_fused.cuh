@@ -345,9 +345,11 @@ __device__ __forceinline__ void issue_tile_async(const StepArgs<float>& a, const
 }
 
 // One tile of the step: the CTA owns cells [i0, i0+TX) x [j0, j0+TY) of the grid
-// described by `a`.  (pi0, pj0), if pi0 >= 0, is a later tile of the same grid:
-// its rows are prefetched into L2 when `pf` is set, and with PIPE its raw input
-// is copied asynchronously into the D region once this tile no longer needs it.
+// described by `a`.  (pi0, pj0), if pi0 >= 0, is a later tile, of the same grid
+// unless `na` describes another one (with tensor maps `ntm`): its rows are
+// prefetched into L2 when `pf` is set (same grid only), and with PIPE its raw
+// input is copied asynchronously into the D region once this tile no longer
+// needs it.
 // With PIPE this tile's own input is already on its way there
 // (issue_tile_async); false means the wait for it timed out (flagged).  With
 // INTER the tile also stores the intermediates of its owned cells that the
@@ -357,7 +359,9 @@ __device__ __forceinline__ void issue_tile_async(const StepArgs<float>& a, const
 // returns after the point updates, for the adjoint's reverse sweep of the tile.
 template <int TX, int TY, int NT, bool COMP, bool PIPE, bool INTER = false, bool ADJ = false>
 __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc, int i0, int j0,
-                                           int pi0, int pj0, bool pf) {
+                                           int pi0, int pj0, bool pf,
+                                           const StepArgs<float>* na = nullptr,
+                                           const TileMaps* ntm = nullptr) {
   using G = FusedGeom<TX, TY>;
   constexpr int CW = G::CW, CH = G::CH, DCW = G::DCW, PW = G::PW;
   constexpr int WPL = G::WPL, DPL = G::DPL, PPL = G::PPL;
@@ -765,7 +769,15 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
   __syncthreads();  // W and D are dead from here
   // the next tile's input streams into D while the fluxes and averages are stored
   if constexpr (PIPE) {
-    if (pi0 >= 0) issue_tile_async<TX, TY, NT, COMP>(a, pc, pi0, pj0, D);
+    if (pi0 >= 0) {
+      if (na) {
+        PipeCtx q = pc;
+        q.tm = ntm;
+        issue_tile_async<TX, TY, NT, COMP>(*na, q, pi0, pj0, D);
+      } else {
+        issue_tile_async<TX, TY, NT, COMP>(a, pc, pi0, pj0, D);
+      }
+    }
   }
 #pragma unroll
   for (int k = 0; k < PERE; ++k) {
@@ -876,6 +888,47 @@ __global__ void __launch_bounds__(NT, MINB)
   const int4 t = tiles[blockIdx.x];
   PipeCtx none = {nullptr, 0u, 0u};
   fused_tile<TX, TY, NT, COMP, false>(args[t.x], none, t.y, t.z, -1, -1, false);
+}
+
+// Batched persistent pipelined form: CTA b steps through entries b, b + G, ...
+// of the tile table (G = gridDim.x); the raw input of its next tile, of
+// whichever grid, is staged while the current one stores its averages.  maps,
+// if not null, holds the tensor maps of every grid's current input planes
+// (maps[grid]); every grid meets the conditions of issue_tile_async.
+template <int TX, int TY, int NT, int MINB, bool COMP>
+__global__ void __launch_bounds__(NT, MINB)
+    k_fused_step_batch_pipe(const StepArgs<float>* __restrict__ args,
+                            const int4* __restrict__ tiles, int ntiles,
+                            const TileMaps* __restrict__ maps) {
+  using G = FusedGeom<TX, TY>;
+  extern __shared__ __align__(16) float4 smem4[];
+  float* S = reinterpret_cast<float*>(smem4 + 4 * G::WPL);
+  const bool tma = maps && G::W_BYTES % 128 == 0 && (smem_addr(smem4) & 127u) == 0;
+  PipeCtx pc;
+  pc.tm = nullptr;
+  pc.bar = smem_addr(reinterpret_cast<char*>(smem4) + G::SMEM);
+  pc.phase = 0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pc.bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int t = blockIdx.x;
+  if (t < ntiles) {
+    const int4 e = tiles[t];
+    pc.tm = tma ? &maps[e.x] : nullptr;
+    issue_tile_async<TX, TY, NT, COMP>(args[e.x], pc, e.y, e.z, S);
+  }
+  for (; t < ntiles; t += gridDim.x) {
+    const int4 e = tiles[t];
+    const int nt = t + gridDim.x;
+    const int4 ne = nt < ntiles ? tiles[nt] : make_int4(0, -1, -1, 0);
+    // the current tile was staged with its own grid's maps
+    pc.tm = tma ? &maps[e.x] : nullptr;
+    if (!fused_tile<TX, TY, NT, COMP, true>(args[e.x], pc, e.y, e.z, ne.y, ne.z, false,
+                                            &args[ne.x], tma ? &maps[ne.x] : nullptr))
+      break;
+  }
 }
 
 constexpr int FUSED_TX = AF_FUSED_TX, FUSED_TY = AF_FUSED_TY, FUSED_NT = AF_FUSED_NT;

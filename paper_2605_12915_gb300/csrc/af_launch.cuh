@@ -96,13 +96,16 @@ inline cudaError_t launch_fused_step(cudaStream_t s, const StepArgs<float>& a, b
   return cudaGetLastError();
 }
 
-// Tile geometries available to the batched launch (the autotuner picks one).
+// Tile geometries available to the batched launch (the autotuner picks one):
+// one CTA per tile of 32x32, 24x16 or 16x16 cells, or (pipe) persistent CTAs
+// stepping through the 32x32 tiles with the next tile staged asynchronously.
 struct BatchGeometry {
-  int tx, ty, nt, minb;
+  int tx, ty, nt, minb, pipe;
 };
-constexpr int N_BATCH_GEOMS = 3;
-constexpr BatchGeometry BATCH_GEOMS[N_BATCH_GEOMS] = {{32, 32, 512, 1}, {24, 16, 256, 2},
-                                                      {16, 16, 256, 3}};
+constexpr int N_BATCH_GEOMS = 4;
+constexpr BatchGeometry BATCH_GEOMS[N_BATCH_GEOMS] = {
+    {32, 32, 512, 1, 0}, {24, 16, 256, 2, 0}, {16, 16, 256, 3, 0},
+    {FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, 1}};
 
 template <int TX, int TY, int NT, int MINB, bool COMP>
 inline cudaError_t launch_batch_geom(cudaStream_t s, const StepArgs<float>* args,
@@ -115,13 +118,28 @@ inline cudaError_t launch_batch_geom(cudaStream_t s, const StepArgs<float>* args
   return cudaGetLastError();
 }
 
+// The persistent form: `ctas` CTAs over the tile table; maps (device, one
+// TileMaps per grid) or null for cp.async staging only.
+template <bool COMP>
+inline cudaError_t launch_batch_pipe(cudaStream_t s, const StepArgs<float>* args,
+                                     const int4* tiles, int ntiles, const TileMaps* maps,
+                                     int ctas) {
+  using G = FusedGeom<FUSED_TX, FUSED_TY>;
+  constexpr auto kern = k_fused_step_batch_pipe<FUSED_TX, FUSED_TY, FUSED_NT, AF_FUSED_MINB, COMP>;
+  const cudaError_t e = allow_smem<kern>(G::SMEM_PIPE);
+  if (e != cudaSuccess) return e;
+  kern<<<ntiles < ctas ? ntiles : ctas, FUSED_NT, G::SMEM_PIPE, s>>>(args, tiles, ntiles, maps);
+  return cudaGetLastError();
+}
+
 template <bool COMP>
 inline cudaError_t launch_batch(int geom, cudaStream_t s, const StepArgs<float>* args,
-                                const int4* tiles, int ntiles) {
+                                const int4* tiles, int ntiles, const TileMaps* maps, int ctas) {
   switch (geom) {
     case 0: return launch_batch_geom<32, 32, 512, 1, COMP>(s, args, tiles, ntiles);
     case 1: return launch_batch_geom<24, 16, 256, 2, COMP>(s, args, tiles, ntiles);
-    default: return launch_batch_geom<16, 16, 256, 3, COMP>(s, args, tiles, ntiles);
+    case 2: return launch_batch_geom<16, 16, 256, 3, COMP>(s, args, tiles, ntiles);
+    default: return launch_batch_pipe<COMP>(s, args, tiles, ntiles, maps, ctas);
   }
 }
 

@@ -82,6 +82,14 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu(libaf, case):
     assert rc == AF_ERR_ARG and not h.value
 
 
+def test_binding_constants_match_the_header():
+    import paper_2605_12915_gb300 as af
+    text = open(HEADER).read()
+    assert int(re.search(r"#define AF_BATCH_GEOMS (\d+)", text).group(1)) == af.AF_BATCH_GEOMS
+    assert int(re.search(r"AF_NINV = (\d+)", text).group(1)) == af.AF_NINV
+    assert int(re.search(r"AF_ERR_TIMEOUT = (\d+)", text).group(1)) == af.AF_ERR_TIMEOUT
+
+
 def test_calls_on_a_null_handle_are_refused(libaf):
     from paper_2605_12915_gb300 import AF_ERR_ARG
     libaf.af_step.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32]
