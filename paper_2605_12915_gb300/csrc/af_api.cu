@@ -804,6 +804,10 @@ void af_destroy(af_handle* h) {
   if (!h) return;
   DeviceGuard guard(h->device);
   cudaStreamSynchronize(h->stream);
+  if (h->aux) {  // an exchange's outgoing copy may still read xstaging
+    cudaStreamSynchronize(h->aux);
+    cudaStreamSynchronize(h->aux_in);
+  }
   if (h->arena) cudaFree(h->arena);
   if (h->staging) cudaFree(h->staging);
   if (h->d_flags) cudaFree(h->d_flags);
@@ -812,8 +816,6 @@ void af_destroy(af_handle* h) {
   if (h->adj_arena) cudaFree(h->adj_arena);
   if (h->xstaging) cudaFree(h->xstaging);
   if (h->aux) {
-    cudaStreamSynchronize(h->aux);
-    cudaStreamSynchronize(h->aux_in);
     cudaStreamDestroy(h->aux);
     cudaStreamDestroy(h->aux_in);
     cudaEventDestroy(h->ev_fork);
