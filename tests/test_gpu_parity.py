@@ -478,4 +478,14 @@ def test_exchange_chain_through_pinned_buffers(precision):
     assert np.array_equal(A.numpy(), s1)
     assert np.array_equal(C.numpy(), s2)
     assert np.array_equal(s.state(), q_round)
+    # a longer stream: each step's result out, the same input back in, the
+    # outputs alternating between two buffers (both export buffers in turn)
+    outs = [torch.empty_like(A).pin_memory() for _ in range(2)]
+    src = torch.from_numpy(P.state.copy()).pin_memory()
+    s.set_state(src)
+    for i in range(5):
+        s.step(P.dt, 1)
+        s.exchange(outs[i % 2], src)
+    s.sync()
+    assert np.array_equal(outs[0].numpy(), s1) and np.array_equal(outs[1].numpy(), s1)
     s.close()
