@@ -610,7 +610,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int t = threadIdx.x + k * NT;
-      if (t >= NPTS) break;
+      if (k >= NPTS / NT && t >= NPTS) break;  // rounds k < NPTS / NT are full (NT threads)
       int fam, px, py;
       point_item<PW, G::PH>(t, fam, px, py);
       const int ox = fam == 2 ? 1 : 0, oy = fam == 1 ? 1 : 0;
@@ -686,7 +686,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
 #pragma unroll
       for (int k = 0; k < PER; ++k) {
         const int t = threadIdx.x + k * NT;
-        if (t >= NPTS) break;
+        if (k >= NPTS / NT && t >= NPTS) break;
         int fam, px, py;
         point_item<PW, G::PH>(t, fam, px, py);
         P[fam * PPL + py * PW + px] = res[k];
@@ -724,7 +724,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
 #pragma unroll
   for (int k = 0; k < PERE; ++k) {
     const int t = threadIdx.x + k * NT;
-    if (t >= NE) break;
+    if (k >= NE / NT && t >= NE) break;  // rounds k < NE / NT are full (NT threads)
     const bool vert = t < NVE;
     int ex, ey;  // row chunks of each edge family first
     if (vert)
@@ -782,7 +782,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
 #pragma unroll
   for (int k = 0; k < PERE; ++k) {
     const int t = threadIdx.x + k * NT;
-    if (t >= NE) break;
+    if (k >= NE / NT && t >= NE) break;
     int ex, ey, e;  // vertical edge ey PW + ex, horizontal NVE + ey TX + ex
     if (t < NVE) {
       chunked_xy<PW, TY>(t, ex, ey);
