@@ -10,7 +10,8 @@ value      device-timed cell-updates/s of K steps (CUDA events on the solver's
 e2e        the same metric through the public API with host buffers: every step
            copies its state in from pinned host memory, advances it and copies
            the result back out (af_exchange_state overlaps one step's outgoing
-           copy with the next step's incoming one).
+           copy with the next step's incoming one); the median of three timed
+           runs (max over ranks).
 roofline   the dominant kernel (the fused step kernel), timed per launch with CUDA
            events: its algorithmic FP32 lane operations per launch / duration
            against 152 SMs x 128 FP32 lanes x SM clock ("alu", the bound), and
@@ -47,7 +48,7 @@ def parse():
     p.add_argument("--precision", default="fp32_comp", choices=["fp32", "fp32_comp", "fp64"])
     p.add_argument("--n", type=int, default=N_CELLS_SIDE)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--e2e-steps", type=int, default=50)
     p.add_argument("--kernel-reps", type=int, default=20)
     p.add_argument("--fp64-steps", type=int, default=100,
                    help="steps of the FP64 comparison run (0: skip)")
@@ -317,13 +318,20 @@ def main():
         torch.cuda.synchronize()
 
     e2e_run(2)  # first use allocates the exchange's staging buffer and streams
-    barrier()
-    t0 = time.perf_counter()
-    e2e_run(e2e_steps)
-    e2e_el = time.perf_counter() - t0
-    e2e = {"value": N * e2e_steps * world / e2e_el, "unit": UNIT,
+    # three timed runs, the median (the host side of the link is shared with
+    # other work on the node and varies from run to run)
+    runs = []
+    for _ in range(3):
+        barrier()
+        t0 = time.perf_counter()
+        e2e_run(e2e_steps)
+        runs.append(time.perf_counter() - t0)
+    e2e_ms, e2e_value = aggregate(1e3 * sorted(runs)[1], N, e2e_steps, world, "cuda")
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(host_in.numel() * 8),
-           "d2h_bytes_per_step": int(host_out.numel() * 8)}
+           "d2h_bytes_per_step": int(host_out.numel() * 8),
+           "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps,
+           "runs_ms_per_step": [round(1e3 * r / e2e_steps, 3) for r in runs]}
 
     hbm, peak_kind = peaks()
     bytes_per_cell = {"fp32": 128, "fp32_comp": 160, "fp64": 256}[args.precision]
