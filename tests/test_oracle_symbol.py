@@ -10,7 +10,12 @@ the 16x16 Fourier symbol of oracle/symbol.py (Appendix D construction):
   nu_crit close to the printed 0.195185 (Sec. 5.2); the crossing is computed
   with the smallest wave number kappa = 0.02, where |g| - 1 is resolved in FP64;
 * RB-TAI's sampled powers through 1000 steps stay bounded near the printed
-  maximum norm 3.87 at nu = 0.25 (Sec. 5.2).
+  maximum norm 3.87 at nu = 0.25 (Sec. 5.2);
+* the one-step pressure gain of the right-running acoustic branch at the
+  vertical-edge midpoint (Sec. 5.3, Eq. pressure-response): its largest
+  distance from the exact gain over all directions at kappa = 1 equals the
+  four printed values for nu = 0.2 ... 0.5 to their printed digits
+  (tests/golden/sec5_3_tai_pressure_gain_maxima.txt).
 """
 import numpy as np
 import pytest
@@ -124,3 +129,48 @@ def test_tai_power_norms_stay_bounded(orc, sym):
             best = max(best, float(np.max(np.linalg.norm(P, ord=2, axis=(1, 2)))))
     print("RB-TAI max ||G^n||, n <= 1000:", best, "(printed 3.87)")
     assert 3.7 < best < 4.0, best
+
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                    "sec5_3_tai_pressure_gain_maxima.txt")
+
+
+def _exact_right_running(xi, eta, bg, gamma):
+    """The exact right-running acoustic plane wave of unit pressure on the
+    background, as the 16 Fourier amplitudes of the symbol: primitive
+    perturbation (1/c^2, n/(rho0 c), 1), its cell average (the product of the
+    two one-dimensional averages of the phase) and the node values of the
+    vertex, vertical-edge and horizontal-edge families."""
+    c = np.sqrt(gamma * bg["p0"] / bg["rho0"])
+    kap = np.hypot(xi, eta)
+    W = np.array([1 / c ** 2, xi / kap / (bg["rho0"] * c), eta / kap / (bg["rho0"] * c), 1.0],
+                 dtype=complex)
+
+    def mean_phase(z):
+        return 1.0 if abs(z) < 1e-12 else (np.exp(1j * z) - 1) / (1j * z)
+
+    return np.concatenate([W * mean_phase(xi) * mean_phase(eta), W,
+                           W * np.exp(0.5j * eta), W * np.exp(0.5j * xi)])
+
+
+def test_tai_pressure_gain_matches_printed_maxima(orc, sym):
+    """Reading: the background is the packet background of Sec. 4.2 and the
+    exact gain of the branch on it carries the background's advection as well
+    as the acoustic phase nu kappa: exp(-i (nu kappa + (dt/h) u0 . (xi, eta)))."""
+    gamma, kap = 1.4, 1.0
+    bg = sym.packet_background()
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    th = np.linspace(0.0, 2 * np.pi, 1441)[:-1]
+    xi, eta = kap * np.cos(th), kap * np.sin(th)
+    for nu_s, printed_s in rows:
+        nu, printed = float(nu_s), float(printed_s)
+        S = sym.Symbol(nu, gamma=gamma, variant=orc.TAI, **bg)
+        G = S.matrix(xi, eta)
+        worst = 0.0
+        for k in range(th.size):
+            q = _exact_right_running(xi[k], eta[k], bg, gamma)
+            g = (G[k] @ q)[11] / q[11]  # pressure at the vertical-edge midpoint
+            g_ex = np.exp(-1j * (nu * kap + S.lam * (bg["u0"] * xi[k] + bg["v0"] * eta[k])))
+            worst = max(worst, abs(g - g_ex))
+        print("nu %.1f: max |g - g_ex| = %.4e (printed %.2e)" % (nu, worst, printed))
+        assert abs(worst - printed) <= 5e-6, (nu, worst, printed)  # half a printed unit
