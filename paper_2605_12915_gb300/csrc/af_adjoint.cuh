@@ -98,6 +98,16 @@ __device__ __forceinline__ void add4_always(double* p, double a, double b, doubl
   atomicAdd(p + 3, d);
 }
 
+// clears the 4-wide record at p once its consumer has read it, so that the
+// records start the next adjoint step at zero without a separate clearing pass
+__device__ __forceinline__ void zero4(float* p) {
+  *reinterpret_cast<float4*>(p) = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void zero4(double* p) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(0.0, 0.0);
+  reinterpret_cast<double2*>(p)[1] = make_double2(0.0, 0.0);
+}
+
 // adds (a, b, c, d) to the 4-wide record at p (16-byte aligned)
 __device__ __forceinline__ void add4(float* p, float a, float b, float c, float d) {
   if (a != 0.f || b != 0.f || c != 0.f || d != 0.f)
@@ -500,7 +510,7 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
   bool any = false;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
-    const T* rec = v.lam + (size_t)(LAM_INC + 4 * (4 * s + FAM)) * ps + 4 * id;
+    T* rec = v.lam + (size_t)(LAM_INC + 4 * (4 * s + FAM)) * ps + 4 * id;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       ld[s][k] = rec[k];
@@ -508,6 +518,8 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
     }
   }
   if (!any) return;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) zero4(v.lam + (size_t)(LAM_INC + 4 * (4 * s + FAM)) * ps + 4 * id);
   const Prim<T> wk = node_w(v, FAM, id);
   const T rk = v.gas.rho_ref + wk.r, pk = v.gas.p_ref + wk.p;
   const T c = sqrt(v.gas.gamma * pk / rk);
@@ -585,9 +597,10 @@ __global__ void k_adj_center(const __grid_constant__ AdjView<T> v) {
   const size_t ps = v.ps;
   if (i < v.nx && j < v.ny) {
     const size_t id = (size_t)j * v.nx + i;
-    const T* lc = v.lam + (size_t)(LAM_NODE + 12) * ps + 4 * id;  // the centre node's record
+    T* lc = v.lam + (size_t)(LAM_NODE + 12) * ps + 4 * id;  // the centre node's record
     const T lw[4] = {lc[0], lc[1], lc[2], lc[3]};
     if (lw[0] != T(0) || lw[1] != T(0) || lw[2] != T(0) || lw[3] != T(0)) {
+      zero4(lc);
       const Gas<T>& g = v.gas;
       // the recovered centre (rho~, u, v, p~) is W(U_c); lambda_U = (dW/dU)^T lambda_W
       const T rho = g.rho_ref + v.scr[id], u = v.scr[ps + id], w = v.scr[2 * ps + id];
@@ -960,9 +973,10 @@ __global__ void k_adj_out(const __grid_constant__ AdjView<T> v,
     for (int k = 0; k < 4; ++k) o.dst[k][t] = (double)v.lam[(size_t)(LAM_OUT + k) * v.ps + t];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      const T* rec = v.lam + (size_t)(LAM_NODE + 4 * f) * v.ps + 4 * t;
+      T* rec = v.lam + (size_t)(LAM_NODE + 4 * f) * v.ps + 4 * t;
 #pragma unroll
       for (int k = 0; k < 4; ++k) o.dst[4 + 4 * f + k][t] = (double)rec[k];
+      zero4(rec);
     }
   }
 }

@@ -49,6 +49,8 @@ struct af_handle {
   int tma;               // 1: the pipelined kernel stages interior tiles by tensor copies
   int zero_copy;         // 1: pinned host planes are converted in place (AF_ZERO_COPY=0: copies)
   void* adj_arena;       // adjoint arena (lazy): LAM_PLANES planes, see AdjView
+  int adj_clean;         // 1: its node and increment records are zero (left so by
+                         // the consumers of the last completed adjoint step)
   double* xstaging;      // 16 FP64 planes of af_exchange_state's outgoing state (lazy)
   cudaStream_t aux;      // af_exchange_state: outgoing copies (lazy)
   cudaStream_t aux_in;   // af_exchange_state: incoming copies (lazy)
@@ -339,6 +341,14 @@ bool planes_overlap(const af_state_f64* a, const af_state_f64* b, size_t bytes) 
 extern "C" af_status af_sync(af_handle* h);
 namespace {
 
+// End of an adjoint step: every kernel ran, so the records are clear again
+// (unless the stream failed).
+af_status adjoint_done(af_handle* h) {
+  const af_status st = af_sync(h);
+  h->adj_clean = (st != AF_ERR_CUDA && st != AF_ERR_STATE) ? 1 : 0;
+  return st;
+}
+
 template <typename T, bool COMP>
 af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const af_state_f64* lout,
                        af_memory where) {
@@ -385,9 +395,14 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
   if constexpr (std::is_same<T, float>::value) {
     const char* fz = getenv("AF_ADJ_FUSED");
     if (h->fused && h->pipe_ctas > 0 && pipe_eligible(f) && !(fz && fz[0] == '0')) {
-      // node and increment records start at zero (planes LAM_NODE ... LAM_INC + 31)
-      if (cudaMemsetAsync(v.lam + (size_t)LAM_NODE * v.ps, 0, plane * 48, s) != cudaSuccess ||
-          launch_fused_adjoint<COMP>(s, f, h->pipe_ctas, h->tma ? &h->tmaps[h->cur] : nullptr,
+      // node and increment records start at zero (planes LAM_NODE ... LAM_INC + 31):
+      // cleared here only after an incomplete step or on first use, since
+      // their consumers clear them as they read them
+      if (!h->adj_clean &&
+          cudaMemsetAsync(v.lam + (size_t)LAM_NODE * v.ps, 0, plane * 48, s) != cudaSuccess)
+        return cuda_fail(h);
+      h->adj_clean = 0;
+      if (launch_fused_adjoint<COMP>(s, f, h->pipe_ctas, h->tma ? &h->tmaps[h->cur] : nullptr,
                                      v) != cudaSuccess)
         return cuda_fail(h);
       k_adj_acoustic<0, T><<<grd, blk, 0, s>>>(v);
@@ -405,7 +420,7 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
                               sizeof(double) * h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return cuda_fail(h);
       if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
-      return af_sync(h);
+      return adjoint_done(h);
     }
   }
   // the stage-by-stage sweep reads lambda^{n+1} in the working precision
@@ -433,9 +448,12 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
     k_points<2, T><<<grd, blk, 0, s>>>(f);
   }
   // reverse sweep: the centre and increment records start at zero (planes
-  // LAM_NODE + 12 ... LAM_INC + 31 are contiguous)
-  if (cudaMemsetAsync(v.lam + (size_t)(LAM_NODE + 12) * v.ps, 0, plane * 36, s) != cudaSuccess)
+  // LAM_NODE + 12 ... LAM_INC + 31 are contiguous; the sweep writes the other
+  // node records before adding to them)
+  if (!h->adj_clean &&
+      cudaMemsetAsync(v.lam + (size_t)(LAM_NODE + 12) * v.ps, 0, plane * 36, s) != cudaSuccess)
     return cuda_fail(h);
+  h->adj_clean = 0;
   k_adj_flux<T><<<grd, blk, 0, s>>>(v);
   k_adj_points<0, T><<<grd, blk, 0, s>>>(v);
   k_adj_points<1, T><<<grd, blk, 0, s>>>(v);
@@ -456,7 +474,7 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
                           sizeof(double) * h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return cuda_fail(h);
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
-  return af_sync(h);
+  return adjoint_done(h);
 }
 
 }  // namespace
