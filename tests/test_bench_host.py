@@ -1,0 +1,58 @@
+"""Host-side logic of bench.py (no GPU): the staleness guard of the recorded ncu
+traffic (a hash of the fused kernel's code, blind to comments), the scaling of
+that traffic to a launch, and the per-field relative L-inf of FP32 against FP64
+(velocity and momentum taken as vectors)."""
+import os
+import shutil
+
+import numpy as np
+
+import bench
+
+
+def _copy_sources(tmp_path):
+    for f in bench.FUSED_SOURCES:
+        dst = tmp_path / f
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, f), dst)
+    return tmp_path
+
+
+def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    root = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h0 = bench.fused_source_hash()
+    target = root / bench.FUSED_SOURCES[0]
+    text = target.read_text()
+    target.write_text("// a new leading comment\n/* and a block\n   comment */\n\n" +
+                      text.replace("\n", "\n   ", 1))
+    assert bench.fused_source_hash() == h0
+    target.write_text(text.replace("constexpr int FUSED_TX", "constexpr int  FUSED_TX", 1)
+                      .replace("FUSED_TY = AF_FUSED_TY", "FUSED_TY = AF_FUSED_TY + 0", 1))
+    assert bench.fused_source_hash() != h0
+
+
+def test_recorded_traffic_matches_the_current_kernel_and_scales():
+    # the committed profile was captured from the current kernel sources
+    full = bench.profiled_traffic(4194304)
+    assert full is not None and full > 0
+    assert abs(bench.profiled_traffic(2 * 4194304) - 2 * full) < 1e-6 * full
+
+
+def test_recorded_traffic_is_dropped_when_the_kernel_changed(monkeypatch):
+    monkeypatch.setattr(bench, "fused_source_hash", lambda: "0" * 16)
+    assert bench.profiled_traffic(4194304) is None
+
+
+def test_per_field_error_takes_velocity_as_a_vector():
+    rng = np.random.default_rng(0)
+    b = 1.0 + rng.random((16, 6, 5))
+    b[[1, 5, 9, 13]] = 1.0   # u (and rho u) = 1
+    b[[2, 6, 10, 14]] = 0.0  # v (and rho v) = 0: a per-plane form would divide by 0
+    a = b.copy()
+    a[6] += 1e-3              # v error at the vertices
+    a[3] *= 1 + 2e-4          # energy average
+    # velocity error 1e-3 against |velocity| 1; energy 2e-4 of itself
+    assert abs(bench.rel_linf_fields(a, b) - 1e-3) < 1e-12
+    a[6] = b[6]
+    assert abs(bench.rel_linf_fields(a, b) - 2e-4) < 1e-12
