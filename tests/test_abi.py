@@ -1,7 +1,9 @@
 """Host-side checks of the CUDA library (no GPU needed): it builds for sm_103a,
 loads, and exports every entry point include/af.h declares; the committed
-generated stencil header is what its generator writes; and the generated
-stencil tables, applied on the CPU, reproduce the oracle's acoustic operator.
+generated stencil header is what its generator writes; the generated stencil
+tables, applied on the CPU, reproduce the oracle's acoustic operator; and the
+generated transposed stencils of the adjoint, evaluated on the CPU, are the
+exact transpose of those tables.
 """
 import ctypes
 import os
@@ -179,3 +181,63 @@ def test_generated_tables_match_oracle_operator(orc, fam_name, fam):
         dv = np.sum(pw * (Gp[2] / Z + Guv[2]))
         got = np.array([K[0] + dp, K[1] + du, K[2] + dv])
         assert np.max(np.abs(got - want)) < 1e-12, (r, got, want)
+
+
+def parse_adjoint(fam_name):
+    """The generated transposed stencil af_sac_<fam>_adj as a Python function
+    (lGp, lGuv) -> ({(dx, dy): [lp, lu, lv]}, [lpK, luK, lvK]), by evaluating
+    its statements in order."""
+    body, inside = [], False
+    for line in open(STENCILS):
+        if line.startswith("__device__ __forceinline__ void af_sac_%s_adj(" % fam_name):
+            inside = True
+            continue
+        if inside:
+            if line.startswith("}"):
+                break
+            body.append(line.strip())
+
+    def run(lGp, lGuv):
+        env = {"lGp": lGp, "lGuv": lGuv, "fma": lambda a, b, c: a * b + c, "T": float}
+        out, kk = {}, [0.0, 0.0, 0.0]
+        names = {"lpK": 0, "luK": 1, "lvK": 2}
+        for st in body:
+            m = re.match(r"const T (\w+) = (.*);$", st)
+            if m:
+                env[m.group(1)] = eval(m.group(2), env)
+                continue
+            m = re.match(r"(lpK|luK|lvK) -= (.*);$", st)
+            if m:
+                kk[names[m.group(1)]] -= eval(m.group(2), env)
+                continue
+            m = re.match(r"S\((-?\d+), (-?\d+), (.*)\);$", st)
+            if m:
+                vals = eval("(" + m.group(3) + ")", env)
+                acc = out.setdefault((int(m.group(1)), int(m.group(2))), [0.0, 0.0, 0.0])
+                for k in range(3):
+                    acc[k] += vals[k]
+                continue
+            assert st in ("", "}") or st.startswith("{") or st.startswith("//"), st
+        return out, kk
+    return run
+
+
+@pytest.mark.parametrize("fam_name", ["V", "EV", "EH", "C"])
+def test_generated_transposed_stencils_are_the_adjoint_of_the_tables(fam_name):
+    """<lG, G(data)> = <G^T lG, data> for random data and adjoints: the scatter
+    code of the adjoint is the exact transpose of the generated forward tables
+    (which the previous test pins to the oracle's acoustic operator)."""
+    tables = parse_stencils()[fam_name]
+    adj = parse_adjoint(fam_name)
+    rng = np.random.default_rng(5)
+    for trial in range(3):
+        lat = {(dx, dy): rng.normal(size=3) for dx in range(-4, 5) for dy in range(-4, 5)}
+        K = lat[(0, 0)]
+        Gp, Guv = apply_tables(tables, lat, K)
+        lGp, lGuv = rng.normal(size=(3, 4)), rng.normal(size=(3, 4))
+        lhs = np.sum(lGp * Gp[:, 1:]) + np.sum(lGuv * Guv[:, 1:])
+        out, kk = adj(lGp, lGuv)
+        rhs = float(np.dot(kk, K))
+        for off, vals in out.items():
+            rhs += float(np.dot(vals, lat[off]))
+        assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs)), (trial, lhs, rhs)
