@@ -1,11 +1,13 @@
 """Host-side logic of bench.py (no GPU): the staleness guard of the recorded ncu
 traffic (a hash of the fused kernel's code, blind to comments), the scaling of
 that traffic to a launch, and the per-field relative L-inf of FP32 against FP64
-(velocity and momentum taken as vectors)."""
+(velocity and momentum taken as vectors); the clock summary of the sampled
+nvidia-smi lines; the marshalling of state arrays into the ABI's 16 planes."""
 import os
 import shutil
 
 import numpy as np
+import pytest
 
 import bench
 
@@ -56,3 +58,33 @@ def test_per_field_error_takes_velocity_as_a_vector():
     assert abs(bench.rel_linf_fields(a, b) - 1e-3) < 1e-12
     a[6] = b[6]
     assert abs(bench.rel_linf_fields(a, b) - 2e-4) < 1e-12
+
+
+def test_clock_summary_from_sampled_lines():
+    s = bench.ClockSampler(0)
+    s.lines = ["2070, 2070, Not Active, Not Active, Not Active, Not Active",
+               "1980, 2070, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], 2070, Not Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    out = s.summary()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
+    s.lines = ["1500, 2070, Active, Not Active, Active, Not Active"]
+    assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None,
+                                               "reasons": [], "samples": 0}
+
+
+def test_state_planes_are_marshalled_in_the_documented_order():
+    import paper_2605_12915_gb300 as af
+    arr = np.zeros((16, 3, 5))
+    ptr, dev = af._array_ptr(arr)
+    assert ptr == arr.ctypes.data and not dev
+    st = af._state_struct(ptr, 15)
+    planes = list(st.avg) + list(st.vtx) + list(st.ev) + list(st.eh)
+    assert planes == [ptr + 8 * 15 * p for p in range(16)]
+    with pytest.raises(AssertionError):
+        af._array_ptr(np.zeros((16, 3, 5), dtype=np.float32))
+    with pytest.raises(AssertionError):
+        af._array_ptr(np.zeros((16, 5, 3)).transpose(0, 2, 1))
