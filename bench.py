@@ -210,7 +210,7 @@ def dist_setup(args):
 def _oracle_replica(sample_n, sample_steps, barrier, results):
     """One copy of the oracle sample in its own process (all cores leg)."""
     import oracle
-    from paper_2605_12915_gb300 import inputs as I
+    from workloads import inputs as I
     S = I.shear(n=sample_n)
     barrier.wait()
     t = time.perf_counter()
@@ -232,7 +232,7 @@ def cpu_baseline(P, sample_n=512, sample_steps=6, all_cores=True):
     processes, started by spawn: the oracle is single-threaded and unmodified),
     their cell-updates summed over the slowest copy's time."""
     import oracle
-    from paper_2605_12915_gb300 import inputs as I
+    from workloads import inputs as I
     S = I.shear(n=sample_n)
     t = time.perf_counter()
     oracle.run(S.state, S.grid.h, S.gamma, S.dt, sample_steps)
@@ -266,7 +266,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_2605_12915_gb300 import inputs as I
+    from workloads import inputs as I
     oracle.build()
     n = 128  # bounded sample per step: a 128^2 copy of the workload
     S = I.shear(n=n)
@@ -297,7 +297,7 @@ def main():
         return
     import torch
     import paper_2605_12915_gb300 as af
-    from paper_2605_12915_gb300 import inputs as I
+    from workloads import inputs as I
 
     rank, world, local = dist_setup(args)
     af._build.build()

@@ -9,7 +9,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_2605_12915_gb300 import autograd as AG  # noqa: E402
-from paper_2605_12915_gb300 import inputs as I  # noqa: E402
+from workloads import inputs as I  # noqa: E402
 
 SHAPE = (16, 2, 3)
 N = int(np.prod(SHAPE))

@@ -23,7 +23,7 @@ import numpy as np
 import pytest
 
 import paper_2605_12915_gb300 as af
-from paper_2605_12915_gb300 import inputs as I
+from workloads import inputs as I
 
 pytestmark = pytest.mark.gpu
 

@@ -4,7 +4,7 @@ number), checked on small copies of each workload.  No method arithmetic: the
 recipes only sample analytic initial data."""
 import numpy as np
 
-from paper_2605_12915_gb300 import inputs as I
+from workloads import inputs as I
 
 G = 1.4
 

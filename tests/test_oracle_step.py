@@ -9,7 +9,7 @@ Simpson inversion / Q2 interpolation building blocks (Sec. 2).
 import numpy as np
 import pytest
 
-from paper_2605_12915_gb300 import inputs as I
+from workloads import inputs as I
 
 EPS = 1e-6
 

@@ -20,7 +20,7 @@ the 16x16 Fourier symbol of oracle/symbol.py (Appendix D construction):
 import numpy as np
 import pytest
 
-from paper_2605_12915_gb300 import inputs as I  # noqa: F401  (path set-up)
+from workloads import inputs as I  # noqa: F401  (path set-up)
 
 
 @pytest.fixture(scope="module")
