@@ -22,6 +22,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 TAI = 0
 RB = 1
+FC = 2  # foot-centred exact acoustic update (Appendix C)
 FLAG_CFL = 1
 FLAG_NONPHYSICAL = 2
 FLAG_NONFINITE = 4
@@ -63,6 +64,8 @@ def _load():
         lib.orc_acoustic_increments.restype = i
         lib.orc_sac_node.argtypes = [i, dp, d, d, dp]
         lib.orc_sac_node.restype = None
+        lib.orc_fc_node.argtypes = [i, dp, d, d, d, d, dp]
+        lib.orc_fc_node.restype = None
         lib.orc_sac_block.argtypes = [i, i, i, dp]
         lib.orc_sac_block.restype = None
         lib.orc_recon_eval.argtypes = [i, i, dp, dp, d, d, dp]
@@ -128,6 +131,16 @@ def sac_node(family, cells, r, Z):
     c = np.ascontiguousarray(cells, dtype=np.float64).reshape(-1)
     out = np.empty(3)
     _load().orc_sac_node(family, _ptr(c), r, Z, _ptr(out))
+    return out
+
+
+def fc_node(family, cells, fx, fy, r, Z):
+    """Foot-centred exact frozen acoustic evolution (Appendix C) at the foot
+    F = P + (fx, fy) h of a point of `family` (V, EV or EH); cells as for
+    sac_node, r = c tau / h, Z = rho c.  Returns (p, u, v) at F."""
+    c = np.ascontiguousarray(cells, dtype=np.float64).reshape(-1)
+    out = np.empty(3)
+    _load().orc_fc_node(family, _ptr(c), fx, fy, r, Z, _ptr(out))
     return out
 
 

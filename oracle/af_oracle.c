@@ -21,6 +21,9 @@
  *   RB additive point update .............. Eq. (barsukow-additive)
  *   RB-TAI transported point update ....... Eq. (transported-update); Sec. 6.1
  *                                           steps 1-4
+ *   foot-centred exact acoustic update .... Appendix C, Eqs. (fc-foot-freeze),
+ *                                           (fc-half-footprint),
+ *                                           (fc-moment-families), (fc-role-rows)
  *   space-time Simpson flux + average ..... Sec. 3.1, Eq. (af-average-update);
  *                                           Sec. 6.1
  *   entropy functional .................... Sec. 6 (-int rho log(p/rho^gamma))
@@ -33,6 +36,10 @@
  *  - RB density: rho = rho_f + (p_ac(P) - p(P)) / c_P^2 (closure of Sec. 3.1
  *    inserted in Eq. (barsukow-additive)).
  *  - Foot cell: floor of the foot position in cell units, periodic wrap.
+ *  - Foot-centred update: the linear density closure of Sec. 3.1 frozen at the
+ *    foot, rho = rho_* + (p - p_*)/c_*^2 (Appendix C offers it beside an
+ *    isentropic one); the moments are taken by quadrature of their definition
+ *    (Appendix C derives closed forms, not printed).
  */
 #define _USE_MATH_DEFINES
 #include <complex.h>
@@ -474,6 +481,315 @@ static void increment_eval(int nx, int ny, double *const dfam[4], double X, doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Foot-centred exact frozen acoustic update (Appendix C).  The acoustic    */
+/* disk of radius R = c_* tau is centred at the convective foot F (not at a */
+/* node); the frozen state is the reconstruction at F (Eq. fc-foot-freeze). */
+/* Under the compact footprint condition (Eq. fc-half-footprint) the disk   */
+/* lies in the cells around the target point and is cut only by the grid   */
+/* lines through that point: a vertex disk into up to four fragments, an    */
+/* edge disk into up to two.                                                 */
+/*                                                                           */
+/* The exact solution of frozen linear acoustics u_t + c grad pi = 0,        */
+/* pi_t + c div u = 0 at the centre of the disk, written with the projected-*/
+/* sphere mean S[f](R) = (1/4pi) int_{B1} f(F + R w) Psi(w) dw,              */
+/* Psi = 2 (1 - |w|^2)^{-1/2} (the 2D Poisson formula by descent):           */
+/*   pi(F, tau) = d/dR [R S[pi_0](R)] - R S[div u_0](R)                      */
+/*   u(F, tau)  = u_0(F) - R S[grad pi_0](R) + R G(R) + int_0^R G(s) ds,     */
+/*   G_j(s) = (1/4pi) int_{B1} (w_1 d_j u_0 + w_2 d_j v_0)(F + s w) Psi dw,  */
+/* where the second line follows from u_t = -c grad pi, the divergence     */
+/* theorem on the ball of radius s in the z-extended 3D problem, and one    */
+/* integration by parts in s.  For continuous piecewise-Q2 data every term  */
+/* is a sum over fragments of the fragment's polynomial (in monomials about */
+/* F) against the fragment's moments m_ij(R) = int xi^i eta^j Psi over the  */
+/* fragment scaled to the unit disk, their radius derivative and their      */
+/* history integral (Eq. fc-moment-families).  On a node-centred disk the   */
+/* fragments are the wedges of Sec. 3.1 and the sum equals the Appendix D   */
+/* update.  Here the moments are computed by direct quadrature: for every   */
+/* ray from F the radial integrals are closed forms, and the angular        */
+/* integral is taken by tanh-sinh quadrature between the angles at which    */
+/* the ray's clipping changes form.  Lengths are in units of h.             */
+/* ------------------------------------------------------------------------ */
+
+/* int_0^phi sin^k t dt */
+static double sin_power_integral(int k, double phi) {
+  if (k == 0) return phi;
+  if (k == 1) return 1.0 - cos(phi);
+  return -pow(sin(phi), k - 1) * cos(phi) / k + (double)(k - 1) / k * sin_power_integral(k - 2, phi);
+}
+
+/* One fragment: the points x (offsets from F, units of h) with
+ * sgn[c] * (x[axis[c]] - d[c]) >= 0 for its n constraints. */
+typedef struct {
+  int n;
+  int axis[2];
+  double sgn[2], d[2];
+} fc_frag_t;
+
+/* the part [lo, hi] of the ray from F at angle th inside the fragment and the
+ * disk of radius r; 0 if empty */
+static int fc_ray(const fc_frag_t *g, double r, double th, double *lo, double *hi) {
+  double a = 0.0, b = r;
+  double e[2] = {cos(th), sin(th)};
+  for (int c = 0; c < g->n; ++c) {
+    double se = g->sgn[c] * e[g->axis[c]];
+    if (se == 0.0) {
+      if (-g->sgn[c] * g->d[c] < 0.0) return 0;
+      continue;
+    }
+    double t = g->d[c] / e[g->axis[c]];
+    if (se > 0.0) {
+      if (t > a) a = t;
+    } else if (t < b) {
+      b = t;
+    }
+  }
+  if (!(a < b)) return 0;
+  *lo = a;
+  *hi = b;
+  return 1;
+}
+
+/* moment arrays of one fragment of the disk of radius r (units of h):
+ *   m[i][j] = int xi^i eta^j Psi over the fragment scaled to the unit disk,
+ *   E[a][b] = r^-q d/dr (r^{q+1} m_ab(r)), q = a + b,
+ *   H[i][j] = int_0^r s^{i+j-1} m_ij(s) ds (i + j >= 1).
+ * On a ray the fragment is lo <= rho <= hi; with rho = r sin(phi) the radial
+ * parts are sin-power integrals. */
+static void fc_ray_terms(double r, double th, double lo, double hi, int hi_on_circle,
+                         double m[5][5], double E[3][3], double H[5][5]) {
+  double plo = asin(fmin(lo / r, 1.0));
+  double phi_hi = hi_on_circle ? 0.5 * M_PI : asin(fmin(hi / r, 1.0));
+  double K_lo[7], K_hi[7];
+  for (int k = 0; k < 7; ++k) {
+    K_lo[k] = sin_power_integral(k, plo);
+    K_hi[k] = sin_power_integral(k, phi_hi);
+  }
+  double c = cos(th), s = sin(th);
+  double cp[5], sp[5];
+  cp[0] = sp[0] = 1.0;
+  for (int k = 1; k < 5; ++k) {
+    cp[k] = cp[k - 1] * c;
+    sp[k] = sp[k - 1] * s;
+  }
+  /* d/dr of r^k K_k(asin(x/r)) = r^{k-1} [k K_k(phi) - sin^k(phi) tan(phi)] */
+  double tan_lo = lo > 0.0 ? (lo / r) / sqrt(fmax(1.0 - (lo / r) * (lo / r), 0.0)) : 0.0;
+  double tan_hi = hi_on_circle ? 0.0 : (hi / r) / sqrt(fmax(1.0 - (hi / r) * (hi / r), 0.0));
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; i + j < 5; ++j) {
+      int k = i + j + 1;
+      double ang = cp[i] * sp[j];
+      m[i][j] = 2.0 * ang * (K_hi[k] - K_lo[k]);
+      if (i + j >= 1) {
+        int q = i + j;
+        double L_hi = K_hi[q - 1] - K_hi[q + 1], L_lo = K_lo[q - 1] - K_lo[q + 1];
+        H[i][j] = 2.0 * pow(r, q) * ang * (L_hi - L_lo);
+      } else {
+        H[i][j] = 0.0;
+      }
+      if (i < 3 && j < 3) {
+        double v = k * K_hi[k] - k * K_lo[k] + pow(lo / r, k) * tan_lo;
+        if (!hi_on_circle) v -= pow(hi / r, k) * tan_hi;
+        E[i][j] = 2.0 * ang * v;
+      }
+    }
+}
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return x < y ? -1 : x > y;
+}
+
+static void fc_fragment_moments(const fc_frag_t *g, double r, double m[5][5], double E[3][3],
+                                double H[5][5]) {
+  memset(m, 0, sizeof(double) * 25);
+  memset(E, 0, sizeof(double) * 9);
+  memset(H, 0, sizeof(double) * 25);
+  /* angles where the ray's clipping changes form */
+  double br[16];
+  int nb = 0;
+  for (int k = 0; k <= 4; ++k) br[nb++] = 0.5 * M_PI * k;
+  for (int c = 0; c < g->n; ++c) {
+    double d = g->d[c];
+    if (fabs(d) < r) {
+      double a = g->axis[c] == 0 ? acos(d / r) : asin(d / r);
+      double a2 = g->axis[c] == 0 ? 2.0 * M_PI - a : M_PI - a;
+      br[nb++] = fmod(a + 2.0 * M_PI, 2.0 * M_PI);
+      br[nb++] = fmod(a2 + 2.0 * M_PI, 2.0 * M_PI);
+    }
+  }
+  if (g->n == 2 && g->axis[0] != g->axis[1]) {
+    double dx = g->axis[0] == 0 ? g->d[0] : g->d[1], dy = g->axis[0] == 0 ? g->d[1] : g->d[0];
+    br[nb++] = fmod(atan2(dy, dx) + 2.0 * M_PI, 2.0 * M_PI);
+  }
+  qsort(br, nb, sizeof(double), cmp_double);
+  /* tanh-sinh rule on each piece: t = k/16, |k| <= 64 */
+  const double hstep = 1.0 / 16.0;
+  for (int p = 0; p + 1 < nb; ++p) {
+    double a = br[p], b = br[p + 1];
+    if (!(b - a > 1e-14)) continue;
+    double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+    for (int k = -64; k <= 64; ++k) {
+      double t = k * hstep;
+      double u = 0.5 * M_PI * sinh(t);
+      double x = tanh(u), w = hstep * 0.5 * M_PI * cosh(t) / (cosh(u) * cosh(u));
+      if (w < 1e-300) continue;
+      double th = mid + half * x, lo, hi;
+      if (!fc_ray(g, r, th, &lo, &hi)) continue;
+      double mm[5][5], ee[3][3], hh[5][5];
+      fc_ray_terms(r, th, lo, hi, hi >= r, mm, ee, hh);
+      double ww = half * w;
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; i + j < 5; ++j) {
+          m[i][j] += ww * mm[i][j];
+          H[i][j] += ww * hh[i][j];
+          if (i < 3 && j < 3) E[i][j] += ww * ee[i][j];
+        }
+    }
+  }
+}
+
+/* Exact frozen acoustic evolution at the centre F of a disk of radius r (units
+ * of h) from fragments of continuous piecewise-Q2 data.  mono[f][k][a][b] is the
+ * polynomial of fragment f, field k = (pi, u, v), in monomials X^a Y^b about F
+ * (units of h).  out = (pi, u, v) at F after the evolution. */
+static void fc_evolve(int nf, const fc_frag_t *frags, double mono[][3][3][3], double r,
+                      double out[3]) {
+  double pi_out = 0.0, du = 0.0, dv = 0.0;
+  /* u_0(F): the constant coefficient of the fragment whose cell holds F (every
+   * constraint holds at the centre; on a grid line either side's polynomial
+   * gives the same value, the data being continuous) */
+  double u0 = 0.0, v0 = 0.0;
+  for (int f = 0; f < nf; ++f) {
+    int holds = 1;
+    for (int c = 0; c < frags[f].n; ++c)
+      if (frags[f].sgn[c] * (0.0 - frags[f].d[c]) < 0.0) holds = 0;
+    if (holds) {
+      u0 = mono[f][1][0][0];
+      v0 = mono[f][2][0][0];
+      break;
+    }
+  }
+  for (int f = 0; f < nf; ++f) {
+    double m[5][5], E[3][3], H[5][5];
+    fc_fragment_moments(&frags[f], r, m, E, H);
+    double(*P)[3] = mono[f][0];
+    double(*U)[3] = mono[f][1];
+    double(*V)[3] = mono[f][2];
+#define MM(i, j) (((i) < 0 || (j) < 0) ? 0.0 : m[i][j])
+#define HH(i, j) (((i) < 0 || (j) < 0) ? 0.0 : H[i][j])
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        int q = a + b;
+        double rq = pow(r, q);
+        /* pi: d/dR [R S[pi_0]] - R S[div u_0] */
+        pi_out += rq * (P[a][b] * E[a][b] - a * U[a][b] * MM(a - 1, b) - b * V[a][b] * MM(a, b - 1));
+        /* velocity: - R S[grad pi_0] + R G(R) + int_0^R G */
+        du += rq * (-a * P[a][b] * MM(a - 1, b) + a * U[a][b] * MM(a, b) +
+                    a * V[a][b] * MM(a - 1, b + 1));
+        dv += rq * (-b * P[a][b] * MM(a, b - 1) + b * U[a][b] * MM(a + 1, b - 1) +
+                    b * V[a][b] * MM(a, b));
+        if (q >= 1) {
+          du += a * U[a][b] * HH(a, b) + a * V[a][b] * HH(a - 1, b + 1);
+          dv += b * U[a][b] * HH(a + 1, b - 1) + b * V[a][b] * HH(a, b);
+        }
+      }
+#undef MM
+#undef HH
+  }
+  out[0] = pi_out / (4.0 * M_PI);
+  out[1] = u0 + du / (4.0 * M_PI);
+  out[2] = v0 + dv / (4.0 * M_PI);
+}
+
+/* The fragments of the disk around a point of family fam whose grid lines lie
+ * at offsets (dX, dY) from F (units of h), in the cell order of `families`
+ * (V: NE, NW, SW, SE; E_v: right, left; E_h: upper, lower). */
+static int fc_fragments(int fam, double dX, double dY, fc_frag_t *g) {
+  static const double sx[4] = {1.0, -1.0, -1.0, 1.0}, sy[4] = {1.0, 1.0, -1.0, -1.0};
+  if (fam == ORC_NODE_V) {
+    for (int k = 0; k < 4; ++k) {
+      g[k].n = 2;
+      g[k].axis[0] = 0;
+      g[k].sgn[0] = sx[k];
+      g[k].d[0] = dX;
+      g[k].axis[1] = 1;
+      g[k].sgn[1] = sy[k];
+      g[k].d[1] = dY;
+    }
+    return 4;
+  }
+  for (int k = 0; k < 2; ++k) {
+    g[k].n = 1;
+    g[k].axis[0] = fam == ORC_NODE_EV ? 0 : 1;
+    g[k].sgn[0] = k == 0 ? 1.0 : -1.0;
+    g[k].d[0] = fam == ORC_NODE_EV ? dX : dY;
+  }
+  return 2;
+}
+
+/* Test hook: the foot-centred evolution for given cell data.  cells as in
+ * orc_sac_node (raw p, u, v nodal values of each adjacent cell of the family,
+ * in the family's cell order); (fx, fy) = F - P in units of h; r = c_* tau / h;
+ * Z = rho_* c_*.  out = (p, u, v) at F. */
+void orc_fc_node(int fam, const double *cells, double fx, double fy, double r, double Z,
+                 double *out) {
+  const family_t *F = &families[fam];
+  fc_frag_t g[4];
+  int nf = fc_fragments(fam, -fx, -fy, g);
+  double mono[4][3][3][3];
+  for (int k = 0; k < nf; ++k)
+    for (int fld = 0; fld < 3; ++fld) {
+      double f[3][3];
+      for (int ix = 0; ix < 3; ++ix)
+        for (int iy = 0; iy < 3; ++iy)
+          f[ix][iy] = cells[27 * k + 9 * fld + 3 * ix + iy] / (fld == 0 ? Z : 1.0);
+      q2_to_monomials(f, F->ox[k] + fx, F->oy[k] + fy, mono[k][fld]);
+    }
+  double o[3];
+  fc_evolve(nf, g, mono, r, o);
+  out[0] = Z * o[0];
+  out[1] = o[1];
+  out[2] = o[2];
+}
+
+/* Foot-centred point value (Appendix C) of family fam at (i, j) for duration
+ * tau, the foot at (Xf, Yf) cell units with reconstruction wf = W_h(F).  The
+ * density follows the acoustic closure of Sec. 3.1 frozen at F,
+ * rho = rho_* + (p - p_*) / c_*^2.  Returns ORC_FLAG_CFL if the compact
+ * footprint condition |F - P|_x + R < h/2, |F - P|_y + R < h/2 fails. */
+static int fc_point(int nx, int ny, double h, double gamma, double tau, int fam, int i, int j,
+                    const double *st, const double *wc, double Xf, double Yf,
+                    const double wf[4], double nw[4]) {
+  const family_t *F = &families[fam];
+  int flags = 0;
+  if (!(wf[0] > 0.0) || !(wf[3] > 0.0)) flags |= ORC_FLAG_NONPHYSICAL;
+  double cs = sqrt(gamma * wf[3] / wf[0]);
+  double Z = wf[0] * cs;
+  double r = cs * tau / h;
+  double X = i + F->px, Y = j + F->py;
+  double fx = Xf - X, fy = Yf - Y; /* F - P, units of h */
+  if (!(fabs(fx) + r < 0.5) || !(fabs(fy) + r < 0.5)) flags |= ORC_FLAG_CFL;
+  double cells[4 * 27];
+  for (int k = 0; k < F->nw; ++k) {
+    double f[3][3][4];
+    cell_nodes(nx, ny, st, wc, i + F->di[k], j + F->dj[k], f);
+    for (int ix = 0; ix < 3; ++ix)
+      for (int iy = 0; iy < 3; ++iy) {
+        cells[27 * k + 0 + 3 * ix + iy] = f[ix][iy][3];
+        cells[27 * k + 9 + 3 * ix + iy] = f[ix][iy][1];
+        cells[27 * k + 18 + 3 * ix + iy] = f[ix][iy][2];
+      }
+  }
+  double out[3];
+  orc_fc_node(fam, cells, fx, fy, r, Z, out);
+  nw[3] = out[0];
+  nw[1] = out[1];
+  nw[2] = out[2];
+  nw[0] = wf[0] + (out[0] - wf[3]) / (cs * cs);
+  return flags;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Point update at tau (Sec. 6.1 steps 3-4; Eq. adv-footpoint;               */
 /* Eq. barsukow-additive for RB).  Writes the four new planes of a family.   */
 /* ------------------------------------------------------------------------ */
@@ -495,7 +811,9 @@ static int point_update(int nx, int ny, double h, double gamma, double tau, int 
       double Xf = X - tau * w1[1] / h, Yf = Y - tau * w1[2] / h;
       orc_recon_eval(nx, ny, st, wc, Xf, Yf, wf);
       double nw[4];
-      if (variant == ORC_TAI) {
+      if (variant == ORC_FC) {
+        flags |= fc_point(nx, ny, h, gamma, tau, fam, i, j, st, wc, Xf, Yf, wf, nw);
+      } else if (variant == ORC_TAI) {
         double d[3];
         increment_eval(nx, ny, dfam, Xf, Yf, d);
         if (!(wf[0] > 0.0) || !(wf[3] > 0.0)) flags |= ORC_FLAG_NONPHYSICAL;
@@ -535,8 +853,9 @@ int orc_step(int nx, int ny, double h, double gamma, double dt, int variant, con
 
   flags |= orc_center_recovery(nx, ny, gamma, in, wc);
 
-  /* acoustic CFL at every node: c_K dt / h <= 1/2 (Sec. 3.1, Sec. 6) */
-  for (int fam = 0; fam < 4; ++fam)
+  /* acoustic CFL at every node: c_K dt / h <= 1/2 (Sec. 3.1, Sec. 6); the
+   * foot-centred update checks its own footprint condition instead */
+  for (int fam = 0; fam < 4 && variant != ORC_FC; ++fam)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         double wk[4];
@@ -552,6 +871,7 @@ int orc_step(int nx, int ny, double h, double gamma, double dt, int variant, con
     for (int fam = 0; fam < 4; ++fam) {
       double *acf = ac + (size_t)fam * 3 * N;
       dfam[fam] = dd + (size_t)fam * 3 * N;
+      if (variant == ORC_FC) continue; /* no nodal increments: the disk sits at the foot */
       flags |= acoustic_outputs(nx, ny, h, gamma, tau, fam, in, wc, acf);
       for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {

@@ -25,6 +25,7 @@ extern "C" {
 
 #define ORC_TAI 0
 #define ORC_RB 1
+#define ORC_FC 2 /* foot-centred exact acoustic update (Appendix C) */
 
 /* error flags returned by orc_step (bitmask) */
 #define ORC_FLAG_CFL 1          /* acoustic CFL c*dt/h > 1/2 at some node */
@@ -40,8 +41,11 @@ extern "C" {
 /* number of invariants written by orc_invariants */
 #define ORC_NINV 12
 
-/* One time step (Sec. 6.1, Algorithm).  in and out hold 16*nx*ny doubles each
- * and must not overlap.  Returns the OR of ORC_FLAG_* seen during the step. */
+/* One time step (Sec. 6.1, Algorithm) with the point update `variant`
+ * (ORC_TAI, ORC_RB or ORC_FC).  in and out hold 16*nx*ny doubles each and must
+ * not overlap.  Returns the OR of ORC_FLAG_* seen during the step; for ORC_FC
+ * ORC_FLAG_CFL reports the compact footprint condition of Appendix C instead
+ * of the nodal acoustic CFL. */
 int orc_step(int nx, int ny, double h, double gamma, double dt, int variant,
              const double *in, double *out);
 
@@ -66,6 +70,15 @@ int orc_acoustic_increments(int nx, int ny, double h, double gamma, double tau, 
  * Wedge order -- V: NE, NW, SW, SE; E_v: right, left; E_h: upper, lower; C: full disk.
  * r = c_K tau / h, Z = rho_K c_K.  out = (p_ac, u_ac, v_ac). */
 void orc_sac_node(int fam, const double *cells, double r, double Z, double *out);
+
+/* Foot-centred exact frozen acoustic evolution (Appendix C) for the point of
+ * family fam (V or an edge family) whose adjacent cells hold `cells` (layout
+ * and order as in orc_sac_node), the disk of radius r = c_* tau / h centred at
+ * the foot F = P + (fx, fy) h, frozen impedance Z = rho_* c_*.  Valid under the
+ * compact footprint condition |fx| + r < 1/2, |fy| + r < 1/2.
+ * out = (p, u, v) at F after the evolution. */
+void orc_fc_node(int fam, const double *cells, double fx, double fy, double r, double Z,
+                 double *out);
 
 /* The 3x3 monomial block C^Theta_ab of Appendix D for wedge w
  * (0 NE,1 NW,2 SW,3 SE,4 right,5 left,6 upper,7 lower,8 full), ordered
