@@ -17,6 +17,14 @@ roofline   the dominant kernel (the fused step kernel), timed per launch with CU
            against 152 SMs x 128 FP32 lanes x SM clock ("alu", the bound), and
            inside it ("hbm") the algorithmic bytes per launch / duration against
            the measured HBM peak.
+fp64       FP64 throughput of the same workload, its fraction of a measured FP64
+           rate, and FP32 against FP64 after 100 steps (per field and per plane).
+fp32_plain the same workload with plain FP32 averages (no lo words).
+shear2000  the workload at its stated length, 2000 steps: throughput, drift of
+           the conserved totals, change of the entropy functional.
+ensemble   the 256-grid vortex ensemble, one batched launch per step against
+           per-grid launches.
+adjoint    the discrete adjoint step against the forward step.
 cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
 --impl reference  times the oracle itself (this workload has no other
            reference implementation), on rank 0 only.
@@ -52,8 +60,13 @@ def parse():
     p.add_argument("--kernel-reps", type=int, default=20)
     p.add_argument("--fp64-steps", type=int, default=100,
                    help="steps of the FP64 comparison run (0: skip)")
-    p.add_argument("--ensemble", action="store_true",
-                   help="also measure the batched 256-grid vortex ensemble (200 steps)")
+    p.add_argument("--no-ensemble", action="store_true",
+                   help="skip the batched 256-grid vortex ensemble (200 steps)")
+    p.add_argument("--shear-steps", type=int, default=2000,
+                   help="steps of the full-length shear-layer run (conservation drift and "
+                        "entropy; 0: skip)")
+    p.add_argument("--fp32-steps", type=int, default=200,
+                   help="steps of the plain FP32 (uncompensated) leg (0: skip)")
     p.add_argument("--adjoint-steps", type=int, default=5,
                    help="adjoint steps timed against the forward step (0: skip)")
     return p.parse_args()
@@ -77,6 +90,9 @@ def peaks():
 # six point updates of 144, space-time Simpson fluxes of 2 edges 278,
 # compensated average update 148.
 ALU_OPS_PER_CELL = 2365
+# plain FP32 averages: the compensated update (148) is replaced by four
+# three-term updates of the averages (16)
+ALU_OPS_PER_CELL_PLAIN = 2365 - 148 + 16
 FUSED_SOURCES = ["paper_2605_12915_gb300/csrc/af_fused.cuh",
                  "paper_2605_12915_gb300/csrc/af_common.cuh",
                  "paper_2605_12915_gb300/csrc/af_stencils.cuh",
@@ -126,18 +142,71 @@ def profiled_traffic(n_cells):
         return None
 
 
+# NVML clock-event reason bits (nvml.h, nvmlClocksEventReason*)
+_NVML_REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                 "sw_power_cap": 0x4}
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clocks and throttle reasons sampled during a timed region: NVML read
+    directly (ctypes, every `period_s`) when the driver's library is there, else
+    `nvidia-smi -lms 100`.  Both record lines "sm, max, hw_slowdown,
+    hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap" ("Active" /
+    "Not Active"), summarised by summary()."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, uuid=None, period_s=0.002):
         self.index = index
+        self.uuid = uuid
+        self.period_s = period_s
         self.proc = None
+        self.thread = None
+        self.stop = None
+        self.source = None
         self.lines = []
 
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        ok = False
+        if self.uuid:
+            ok = lib.nvmlDeviceGetHandleByUUID(("GPU-" + str(self.uuid)).encode(),
+                                               ctypes.byref(h)) == 0
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(self.index, ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        return lib, h
+
+    def _poll_nvml(self, lib, h):
+        import ctypes
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    get_reasons(h, ctypes.byref(rs)) == 0):
+                flags = ["Active" if rs.value & _NVML_REASONS[k] else "Not Active"
+                         for k in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                   "sw_power_cap")]
+                self.lines.append(", ".join([str(clk.value), str(mx.value)] + flags))
+            self.stop.wait(self.period_s)
+
     def __enter__(self):
+        import threading as th
+        try:
+            lib, h = self._nvml_handle()
+            self.stop = th.Event()
+            self.thread = th.Thread(target=self._poll_nvml, args=(lib, h), daemon=True)
+            self.thread.start()
+            self.source = "nvml"
+            return self
+        except Exception:
+            pass
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
@@ -145,6 +214,7 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            self.source = "nvidia-smi"
         except Exception:
             self.proc = None
         return self
@@ -154,6 +224,9 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        if self.stop is not None:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -177,7 +250,8 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm),
+                "source": self.source}
 
 
 def aggregate(ms_local, n_cells, steps, world, device):
@@ -302,6 +376,9 @@ def main():
     rank, world, local = dist_setup(args)
     af._build.build()
     af.load()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    n_sms = props.multi_processor_count
+    uuid = getattr(props, "uuid", None)
     P = I.shear(n=args.n)
     N = P.grid.nx * P.grid.ny
     stream = torch.cuda.Stream()
@@ -323,7 +400,7 @@ def main():
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local, uuid) as clocks:
         ev0.record(stream)
         solver.step(P.dt, args.steps)
         ev1.record(stream)
@@ -377,7 +454,7 @@ def main():
     ach = bytes_per_cell * N / (kstats["ms_per_launch"] * 1e-3) / 1e9
     csum = clocks.summary()
     sm_hz = 1e6 * (csum["sm_max_mhz"] or 2070.0)
-    alu_peak = 152 * 128 * sm_hz / 1e12
+    alu_peak = n_sms * 128 * sm_hz / 1e12
     alu_ach = ALU_OPS_PER_CELL * N / (kstats["ms_per_launch"] * 1e-3) / 1e12
     hbm_part = {"achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "peak_kind": peak_kind, "bytes_per_cell": bytes_per_cell}
@@ -386,15 +463,20 @@ def main():
         # runs near a tenth of its peak)
         roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "T FP32 op/s",
                 "frac": alu_ach / alu_peak, "ops_per_cell": ALU_OPS_PER_CELL,
-                "peak_kind": "152 SMs x 128 FP32 lanes x max SM clock",
+                "peak_kind": "%d SMs x 128 FP32 lanes x max SM clock" % n_sms,
                 "traffic": profiled_traffic(N), "kernel": kstats["kernel"], "hbm": hbm_part}
     else:
         roof = dict(bound="hbm", traffic=None, kernel=kstats["kernel"], **hbm_part)
+    extras = world == 1  # replicas (N > 1) time the step only
     fp64 = fp64_compare(af, I, P, solver_state_after(af, P, args, stream), args, stream, torch) \
-        if args.fp64_steps > 0 else None
+        if args.fp64_steps > 0 and extras else None
     adjoint = adjoint_cost(af, P, args, stream, torch, kstats["ms_per_launch"]) \
-        if args.adjoint_steps > 0 else None
-    ensemble = ensemble_block(af, I, stream, torch) if args.ensemble else None
+        if args.adjoint_steps > 0 and extras else None
+    ensemble = ensemble_block(af, I, stream, torch) if not args.no_ensemble and extras else None
+    shear_long = shear_long_run(af, P, args.shear_steps, stream, torch, local, uuid) \
+        if args.shear_steps > 0 and extras else None
+    fp32_plain = plain_fp32_leg(af, P, args.fp32_steps, stream, torch, alu_peak, hbm) \
+        if args.fp32_steps > 0 and extras and args.precision == "fp32_comp" else None
     drift = (inv1[:4] - inv0[:4]) / np.array([inv0[0], inv0[0], inv0[0], inv0[3]])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -413,6 +495,8 @@ def main():
             "fp64": fp64,
             "adjoint": adjoint,
             "ensemble": ensemble,
+            "fp32_plain": fp32_plain,
+            "shear2000": shear_long,
             "conservation_drift": [float(x) for x in drift],
             "entropy_change": float(inv1[4] - inv0[4])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -468,6 +552,67 @@ def ensemble_block(af, I, stream, torch, n_problems=256, steps=200):
             "speedup": ms_seq / ms_batch}
 
 
+def shear_long_run(af, P, steps, stream, torch, local, uuid):
+    """The shear-layer workload at its stated length (2000 steps from the initial
+    state, FP32 with compensated averages): device-timed throughput, the drift
+    of the conserved totals and the change of the entropy functional (FP64
+    reductions of the initial and final states)."""
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp32_comp", stream=stream)
+    inv0 = s.invariants()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local, uuid, period_s=0.01) as clk:
+        e0.record(stream)
+        s.step(P.dt, steps)
+        e1.record(stream)
+        e1.synchronize()
+    s.sync()
+    ms = e0.elapsed_time(e1)
+    inv1 = s.invariants()
+    s.close()
+    N = P.grid.nx * P.grid.ny
+    names = af.INVARIANT_NAMES
+    # drift relative to the initial totals; the momentum totals are zero, so
+    # their drift is stated relative to the total mass
+    scale = [inv0[0], inv0[0], inv0[0], inv0[3]]
+    return {"steps": steps, "t_final": steps * P.dt, "ms_per_step": ms / steps,
+            "value": N * steps / (ms * 1e-3), "unit": UNIT, "precision": "fp32_comp",
+            "conservation_drift": {names[k]: float((inv1[k] - inv0[k]) / scale[k])
+                                   for k in range(4)},
+            "entropy": {k: {"initial": float(inv0[i]), "final": float(inv1[i]),
+                            "change": float(inv1[i] - inv0[i])}
+                        for k, i in (("simpson", 4), ("average", 5))},
+            "kinetic_energy": {"initial": float(inv0[6]), "final": float(inv1[6])},
+            "min_rho": float(inv1[8]), "min_p": float(inv1[9]),
+            "clocks": clk.summary()}
+
+
+def plain_fp32_leg(af, P, steps, stream, torch, alu_peak, hbm):
+    """The same workload with plain FP32 averages (no lo words): per-launch time
+    of the fused kernel and its fractions of the FP32-issue and HBM rooflines
+    (128 algorithmic bytes per cell)."""
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp32", stream=stream)
+    s.step(P.dt, 5)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(P.dt, steps)
+    e1.record(stream)
+    e1.synchronize()
+    s.sync()
+    s.close()
+    ms = e0.elapsed_time(e1) / steps
+    N = P.grid.nx * P.grid.ny
+    alu = ALU_OPS_PER_CELL_PLAIN * N / (ms * 1e-3) / 1e12
+    gbs = 128 * N / (ms * 1e-3) / 1e9
+    return {"ms_per_step": ms, "value": N / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "alu": {"achieved": alu, "peak": alu_peak, "frac": alu / alu_peak,
+                    "ops_per_cell": ALU_OPS_PER_CELL_PLAIN, "unit": "T FP32 op/s"},
+            "hbm": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm, "bytes_per_cell": 128,
+                    "unit": "GB/s"}}
+
+
 def adjoint_cost(af, P, args, stream, torch, fwd_ms):
     """Time of one discrete adjoint step (af_adjoint_step, device buffers, same
     precision and workload) against one forward step."""
@@ -512,13 +657,48 @@ def fp64_compare(af, I, P, st32, args, stream, torch):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / args.fp64_steps
     st64 = s.state()
+    e0.record(stream)
+    s.invariants()
+    e1.record(stream)
+    e1.synchronize()
+    inv_ms = e0.elapsed_time(e1)
     s.close()
     num = np.max(np.abs(st32 - st64), axis=(1, 2))
     den = np.maximum(np.max(np.abs(st64), axis=(1, 2)), 1e-300)
-    return {"value": P.grid.nx * P.grid.ny / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+    N = P.grid.nx * P.grid.ny
+    peak = fp64_peak(torch)
+    ach = ALU_OPS_PER_CELL_PLAIN * N / (ms * 1e-3) / 1e12
+    return {"value": N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "steps": args.fp64_steps,
+            "roofline": {"bound": "fp64 alu", "achieved": ach, "unit": "T FP64 op/s",
+                         "ops_per_cell": ALU_OPS_PER_CELL_PLAIN, "peak": peak,
+                         "frac": ach / peak if peak else None,
+                         "peak_kind": "measured: torch float64 matmul 4096^3 (cuBLAS), "
+                                      "multiply-adds counted once"},
+            "invariants_ms": inv_ms,
             "fp32_vs_fp64_rel_linf": rel_linf_fields(st32, st64),
+            "fp32_vs_fp64_rel_linf_per_plane_max": float(np.max(num / den)),
             "fp32_vs_fp64_rel_linf_per_plane": [float(x) for x in num / den]}
+
+
+def fp64_peak(torch, n=4096, reps=3):
+    """Measured FP64 rate of this GPU in T multiply-adds/s (a multiply-add
+    counted once, like the operation counts): the best of `reps` float64
+    matmuls of n^3 through cuBLAS."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return float(n) ** 3 / (best * 1e-3) / 1e12
 
 
 def rel_linf_fields(a, b):

@@ -54,7 +54,14 @@ typedef enum {
 
 typedef enum {
   AF_TAI = 0, /* transported acoustic increments, Eq. (transported-update) */
-  AF_RB = 1   /* additive point update, Eq. (barsukow-additive) */
+  AF_RB = 1,  /* additive point update, Eq. (barsukow-additive) */
+  AF_FC = 2   /* foot-centred exact acoustic update (Appendix C): the acoustic
+                 disk of radius c_* tau centred at the convective foot, state
+                 frozen there, density from the linear closure of Sec. 3.1 at
+                 the foot; FP64 only (an analytical reference: the paper puts
+                 its cost at about 1000x the node-centred update); needs the
+                 compact footprint |F - P| + c_* tau < h/2 per axis
+                 (Eq. fc-half-footprint), else the step reports AF_ERR_CFL */
 } af_variant;
 
 typedef enum { AF_HOST = 0, AF_DEVICE = 1 } af_memory;
@@ -114,8 +121,12 @@ enum {
  * AF_TMA=0 stages every tile by cp.async instead of tensor copies;
  * AF_PREFETCH=0 disables the L2 prefetch of the one-CTA-per-tile kernel;
  * AF_ZERO_COPY=0 copies pinned host planes through a staging buffer instead
- * of converting them in place.  AF_ADJ_FUSED=0, read by each
- * af_adjoint_step call, selects its stage-by-stage sweep. */
+ * of converting them in place; AF_TEST_LATE_WAIT=1 (testing the timeout
+ * path only) makes the handle's first pipelined FP32 step give up its first
+ * wait for a tensor-copied tile at once, so that the step reports
+ * AF_ERR_TIMEOUT (the CTA still drains its copies before it stops).
+ * AF_ADJ_FUSED=0, read by each af_adjoint_step call, selects its
+ * stage-by-stage sweep. */
 af_status af_init(af_handle **out, const af_grid *g, double gamma, const af_state_f64 *state,
                   af_memory where, af_precision prec, af_variant var, void *cuda_stream);
 
@@ -175,7 +186,8 @@ af_status af_reduce_invariants(af_handle *h, double *out);
  * in the FP32 modes on grids the pipelined fused kernel accepts, one launch
  * recomputes each tile's step and reverses its fluxes and point updates in
  * shared memory.  Synchronises the stream; returns the latched device error,
- * if any. */
+ * if any. AF_FC handles are refused with AF_ERR_ARG (no adjoint of the
+ * foot-centred update is provided). */
 af_status af_adjoint_step(af_handle *h, double dt, const af_state_f64 *lam_in,
                           const af_state_f64 *lam_out, af_memory where);
 
@@ -198,11 +210,14 @@ const char *af_status_string(af_status s);
  * static device array of about 6.3 MB that every GPU loading the library holds
  * until the process exits); no cudaMalloc, cudaFree or other allocating call
  * is made.  The first call on a device looks up the work area's address on
- * that device (make it before any stream capture).  Every call shares the one
- * work area: calls that overlap on the GPU (other streams, other threads)
- * race and must be serialised by the caller.  Synchronises `cuda_stream` and
- * returns the step's error status; nx * ny > AF_NOALLOC_MAX_CELLS, or any
- * other invalid argument, returns AF_ERR_ARG without touching the GPU. */
+ * that device; make that first call before any stream capture.  Every call
+ * shares the one work area: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  Every call clears
+ * the work area's error word, enqueues the step on `cuda_stream`, then copies
+ * the error word to the host and synchronises `cuda_stream` before it returns
+ * the step's error status.  nx * ny > AF_NOALLOC_MAX_CELLS, `in` and `out`
+ * sharing any byte, or any other invalid argument returns AF_ERR_ARG without
+ * touching the GPU. */
 af_status af_step_noalloc(const af_grid *g, double gamma, double dt, af_variant var,
                           const af_state_f64 *in, const af_state_f64 *out, void *cuda_stream);
 

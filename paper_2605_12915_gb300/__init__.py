@@ -18,7 +18,7 @@ from . import _build
 AF_OK, AF_ERR_ARG, AF_ERR_CUDA, AF_ERR_ALLOC, AF_ERR_CFL, AF_ERR_NONPHYSICAL, \
     AF_ERR_NONFINITE, AF_ERR_STATE, AF_ERR_TIMEOUT = range(9)
 AF_FP64, AF_FP32, AF_FP32_COMP = 0, 1, 2
-AF_TAI, AF_RB = 0, 1
+AF_TAI, AF_RB, AF_FC = 0, 1, 2
 AF_HOST, AF_DEVICE = 0, 1
 AF_NINV = 12
 AF_BATCH_GEOMS = 4
@@ -26,7 +26,7 @@ INVARIANT_NAMES = ["mass", "mom_x", "mom_y", "energy", "entropy_simpson", "entro
                    "kinetic_energy", "max_wave_speed", "min_rho", "min_p",
                    "vorticity_integral", "flags"]
 PRECISIONS = {"fp64": AF_FP64, "fp32": AF_FP32, "fp32_comp": AF_FP32_COMP}
-VARIANTS = {"tai": AF_TAI, "rb": AF_RB}
+VARIANTS = {"tai": AF_TAI, "rb": AF_RB, "fc": AF_FC}
 
 LIB_PATH = _build.LIB
 

@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libaf.so")
-SOURCES = ["af_api.cu", "af_noalloc.cu"]
+SOURCES = ["af_api.cu", "af_noalloc.cu", "af_fc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,9 +36,22 @@ def build(force=False, verbose=False, extra_flags=()):
     # CTAs compute redundantly (tile-boundary points and edge fluxes) must round
     # identically in every unrolled copy of the code, or conservation breaks;
     # the hot loops use explicit fma() where fusion is wanted.
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
-           "-shared",
-           "-o", LIB + ".tmp", *[os.path.join(CSRC, s) for s in SOURCES], *extra_flags]
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
+             *extra_flags]
+    # one object per translation unit, compiled in parallel, then one link
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(CSRC, "_build", src.replace(".cu", ".o"))
+        os.makedirs(os.path.dirname(obj), exist_ok=True)
+        cmd = [nvcc(), *flags, "-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append(subprocess.Popen(cmd, cwd=CSRC))
+        objs.append(obj)
+    failed = [p.args for p in procs if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, failed[0])
+    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd, cwd=CSRC)

@@ -8,7 +8,10 @@ x0 is a float64 CUDA tensor of shape (16, ny, nx) (the state layout of the
 package).  The forward pass keeps a checkpoint every `checkpoint_every` steps;
 the backward pass walks the segments in reverse, recomputes the states of a
 segment from its checkpoint, and applies the adjoint step to them in reverse.
-Memory: one state per checkpoint plus the states of one segment.
+Memory: one state per checkpoint plus the states of one segment.  The solver
+and the checkpoints live until the backward pass, which releases them: a
+graph is differentiated once (a second backward raises), and a graph that is
+never differentiated holds them until it is garbage-collected.
 """
 import torch
 
@@ -40,6 +43,9 @@ class _Rollout(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g):
+        if ctx.solver is None:
+            raise RuntimeError("rollout supports one backward pass: its solver and checkpoints "
+                               "are released by the first")
         solver, ckpts = ctx.solver, ctx.ckpts
         dt, n_steps, every = ctx.meta
         lam = g.contiguous()

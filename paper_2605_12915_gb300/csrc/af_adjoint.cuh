@@ -902,6 +902,7 @@ __global__ void __launch_bounds__(NT, MINB)
   pc.tm = (use_tma && G::W_BYTES % 128 == 0 && (smem_addr(smem4) & 127u) == 0) ? &tm : nullptr;
   pc.bar = smem_addr(reinterpret_cast<char*>(smem4) + G::SMEM);
   pc.phase = 0;
+  pc.late = 0;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pc.bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

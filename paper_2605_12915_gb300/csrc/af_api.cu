@@ -18,8 +18,14 @@
 #include "af_fused.cuh"
 #include "af_launch.cuh"
 #include "af_adjoint.cuh"
+#include "af_state_util.h"
 
 using namespace af;
+
+namespace af {
+// foot-centred point update of the three point families (af_fc.cu)
+cudaError_t launch_fc_points(const StepArgs<double>& a, dim3 grd, dim3 blk, cudaStream_t s);
+}  // namespace af
 
 struct af_handle {
   int device;
@@ -55,6 +61,8 @@ struct af_handle {
   cudaStream_t aux;      // af_exchange_state: outgoing copies (lazy)
   cudaStream_t aux_in;   // af_exchange_state: incoming copies (lazy)
   cudaEvent_t ev_fork, ev_join, ev_in;
+  int late_once;         // testing only (AF_TEST_LATE_WAIT=1 at af_init): the first
+                         // pipelined step reports its first staged-tile wait as timed out
   int out_pending;       // 1: the outgoing copies of the last exchange may be in flight
   af_state_f64 pending_out;  // ... into these planes
 };
@@ -179,6 +187,7 @@ StepArgs<T> step_args(af_handle* h, double dt) {
   a.gas.p_ref = (T)h->p_ref;
   a.variant = (int)h->var;
   a.prefetch_wave = h->prefetch_wave;
+  a.late_first_wait = 0;
   return a;
 }
 
@@ -187,6 +196,15 @@ void launch_ref_step(af_handle* h, double dt) {
   StepArgs<T> a = step_args<T>(h, dt);
   dim3 blk(32, 8), grd((h->nx + 31) / 32, (h->ny + 7) / 8);
   cudaStream_t s = h->stream;
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->var == AF_FC) {  // foot-centred: no nodal increments, points from the foot disks
+      k_center<T, COMP><<<grd, blk, 0, s>>>(a);
+      launch_fc_points(a, grd, blk, s);
+      k_flux<T><<<grd, blk, 0, s>>>(a);
+      k_average<T, COMP><<<grd, blk, 0, s>>>(a);
+      return;
+    }
+  }
   k_center<T, COMP><<<grd, blk, 0, s>>>(a);
   k_acoustic<0, T><<<grd, blk, 0, s>>>(a);
   k_acoustic<1, T><<<grd, blk, 0, s>>>(a);
@@ -203,16 +221,22 @@ void launch_step(af_handle* h, double dt) {
   switch (h->prec) {
     case AF_FP64: launch_ref_step<double, false>(h, dt); break;
     case AF_FP32:
-      if (h->fused)
-        launch_fused_step<false>(h->stream, step_args<float>(h, dt), h->pipe_ctas > 0,
-                                 h->pipe_ctas, h->tma ? &h->tmaps[h->cur] : nullptr);
-      else launch_ref_step<float, false>(h, dt);
-      break;
     case AF_FP32_COMP:
-      if (h->fused)
-        launch_fused_step<true>(h->stream, step_args<float>(h, dt), h->pipe_ctas > 0,
-                                h->pipe_ctas, h->tma ? &h->tmaps[h->cur] : nullptr);
-      else launch_ref_step<float, true>(h, dt);
+      if (h->fused) {
+        StepArgs<float> a = step_args<float>(h, dt);
+        a.late_first_wait = h->late_once;  // testing only, one step
+        h->late_once = 0;
+        if (h->prec == AF_FP32_COMP)
+          launch_fused_step<true>(h->stream, a, h->pipe_ctas > 0, h->pipe_ctas,
+                                  h->tma ? &h->tmaps[h->cur] : nullptr);
+        else
+          launch_fused_step<false>(h->stream, a, h->pipe_ctas > 0, h->pipe_ctas,
+                                   h->tma ? &h->tmaps[h->cur] : nullptr);
+      } else if (h->prec == AF_FP32_COMP) {
+        launch_ref_step<float, true>(h, dt);
+      } else {
+        launch_ref_step<float, false>(h, dt);
+      }
       break;
   }
 }
@@ -224,12 +248,7 @@ af_status check_state_ptrs(const af_state_f64* s) {
   return AF_OK;
 }
 
-const double* plane_in(const af_state_f64* s, int p) {
-  if (p < 4) return s->avg[p];
-  if (p < 8) return s->vtx[p - 4];
-  if (p < 12) return s->ev[p - 8];
-  return s->eh[p - 12];
-}
+const double* plane_in(const af_state_f64* s, int p) { return state_plane(s, p); }
 
 af_status ensure_staging(af_handle* h) {
   if (h->staging) return AF_OK;
@@ -326,16 +345,6 @@ af_status export_enqueue(af_handle* h, const F64Out& dst) {
   return cudaGetLastError() == cudaSuccess ? AF_OK : cuda_fail(h);
 }
 
-// true when some plane of a and some plane of b share a byte
-bool planes_overlap(const af_state_f64* a, const af_state_f64* b, size_t bytes) {
-  for (int p = 0; p < 16; ++p)
-    for (int q = 0; q < 16; ++q) {
-      const char* x = (const char*)plane_in(a, p);
-      const char* y = (const char*)plane_in(b, q);
-      if (x < y + bytes && y < x + bytes) return true;
-    }
-  return false;
-}
 
 }  // namespace
 extern "C" af_status af_sync(af_handle* h);
@@ -502,7 +511,8 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
   *out = nullptr;
   if (!g || g->nx < 2 || g->ny < 2 || !(g->h > 0.0) || !(gamma > 1.0)) return AF_ERR_ARG;
   if (prec != AF_FP64 && prec != AF_FP32 && prec != AF_FP32_COMP) return AF_ERR_ARG;
-  if (var != AF_TAI && var != AF_RB) return AF_ERR_ARG;
+  if (var != AF_TAI && var != AF_RB && var != AF_FC) return AF_ERR_ARG;
+  if (var == AF_FC && prec != AF_FP64) return AF_ERR_ARG;  // FP64 reference variant only
   if (where != AF_HOST && where != AF_DEVICE) return AF_ERR_ARG;
   if (check_state_ptrs(state) != AF_OK) return AF_ERR_ARG;
   if ((int64_t)g->nx * (int64_t)g->ny > (int64_t)1 << 31) return AF_ERR_ARG;
@@ -542,6 +552,10 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
   {
     const char* zc = getenv("AF_ZERO_COPY");
     h->zero_copy = (zc && zc[0] == '0') ? 0 : 1;
+    // testing the timeout path: the handle's first pipelined step gives up its
+    // first wait for a tensor-copied tile at once (the copies still complete)
+    const char* lw = getenv("AF_TEST_LATE_WAIT");
+    h->late_once = (lw && lw[0] == '1') ? 1 : 0;
   }
   // 2 x 20 state planes + 48 scratch planes, each padded to 256 bytes
   size_t plane = (h->N * h->esize + 255) & ~(size_t)255;
@@ -686,7 +700,7 @@ af_status af_exchange_state(af_handle* h, const af_state_f64* out, const af_stat
   if (!h || check_state_ptrs(out) != AF_OK || check_state_ptrs(in) != AF_OK ||
       (where != AF_HOST && where != AF_DEVICE))
     return AF_ERR_ARG;
-  if (planes_overlap(out, in, sizeof(double) * h->N)) return AF_ERR_ARG;
+  if (state_planes_overlap(out, in, sizeof(double) * h->N)) return AF_ERR_ARG;
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
   if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
@@ -719,7 +733,7 @@ af_status af_exchange_state(af_handle* h, const af_state_f64* out, const af_stat
   }
   // an incoming plane that is also the target of the last exchange's outgoing
   // copies is read after them
-  if (h->out_pending && planes_overlap(&h->pending_out, in, sizeof(double) * h->N) &&
+  if (h->out_pending && state_planes_overlap(&h->pending_out, in, sizeof(double) * h->N) &&
       cudaStreamWaitEvent(h->aux_in, h->ev_join, 0) != cudaSuccess)
     return cuda_fail(h);
   // the staging buffer is idle: every earlier call that used it has synchronised
@@ -808,6 +822,7 @@ af_status af_adjoint_step(af_handle* h, double dt, const af_state_f64* lam_in,
       check_state_ptrs(lam_out) != AF_OK || (where != AF_HOST && where != AF_DEVICE))
     return AF_ERR_ARG;
   if (h->broken) return AF_ERR_STATE;
+  if (h->var == AF_FC) return AF_ERR_ARG;  // no adjoint of the foot-centred update
   DeviceGuard guard(h->device);
   if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
   switch (h->prec) {
@@ -960,6 +975,7 @@ af_status af_batch_init(af_batch** out, int32_t n, const af_grid* grids, double 
   if (!out) return AF_ERR_ARG;
   *out = nullptr;
   if (n < 1 || !grids || !states || (prec != AF_FP32 && prec != AF_FP32_COMP)) return AF_ERR_ARG;
+  if (var != AF_TAI && var != AF_RB) return AF_ERR_ARG;
   af_batch* b = new (std::nothrow) af_batch();
   if (!b) return AF_ERR_ALLOC;
   memset(b, 0, sizeof(*b));

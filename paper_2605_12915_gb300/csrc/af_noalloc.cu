@@ -14,6 +14,7 @@
 
 #include "../../include/af.h"
 #include "af_ref_kernels.cuh"
+#include "af_state_util.h"
 
 using namespace af;
 
@@ -81,6 +82,9 @@ extern "C" af_status af_step_noalloc(const af_grid* g, double gamma, double dt, 
   if ((size_t)g->nx * (size_t)g->ny > kMaxCells) return AF_ERR_ARG;  // beyond the work area
   if (var != AF_TAI && var != AF_RB) return AF_ERR_ARG;
   if (!planes_ok(in) || !planes_ok(out)) return AF_ERR_ARG;
+  // the kernels write `out` while later ones still read `in`
+  if (state_planes_overlap(in, out, sizeof(double) * (size_t)g->nx * (size_t)g->ny))
+    return AF_ERR_ARG;
   double* work = nullptr;
   af_status st = work_area(&work);
   if (st != AF_OK) return st;
@@ -124,6 +128,7 @@ extern "C" af_status af_step_noalloc(const af_grid* g, double gamma, double dt, 
   a.gas.p_ref = 0.0;
   a.variant = (int)var;
   a.prefetch_wave = 0;
+  a.late_first_wait = 0;
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // the work area keeps the previous call's contents: the error word must start at 0

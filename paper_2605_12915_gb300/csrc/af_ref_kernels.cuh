@@ -29,6 +29,8 @@ struct StepArgs {
   Gas<T> gas;
   int variant;        // 0 TAI, 1 RB
   int prefetch_wave;  // fused kernel: blocks per wave for the L2 prefetch (0: none)
+  int late_first_wait;  // pipelined kernels, testing only: each CTA's first wait for a
+                        // tensor-copied tile reports a timeout at once (0: off)
 };
 
 template <typename T>

@@ -58,7 +58,9 @@ _BAD_INIT = {
     "gamma = 1": dict(gamma=1.0),
     "gamma NaN": dict(gamma=float("nan")),
     "unknown precision": dict(prec=3),
-    "unknown variant": dict(var=2),
+    "unknown variant": dict(var=3),
+    "foot-centred variant in FP32": dict(var=2, prec=1),
+    "foot-centred variant in FP32 compensated": dict(var=2, prec=2),
     "unknown memory kind": dict(where=2),
     "null state plane": dict(null_plane=5),
     "more than 2^31 cells": dict(nx=65536, ny=32769),
@@ -90,6 +92,7 @@ def test_binding_constants_match_the_header():
     assert int(re.search(r"#define AF_BATCH_GEOMS (\d+)", text).group(1)) == af.AF_BATCH_GEOMS
     assert int(re.search(r"AF_NINV = (\d+)", text).group(1)) == af.AF_NINV
     assert int(re.search(r"AF_ERR_TIMEOUT = (\d+)", text).group(1)) == af.AF_ERR_TIMEOUT
+    assert int(re.search(r"AF_FC = (\d+)", text).group(1)) == af.AF_FC
 
 
 def test_calls_on_a_null_handle_are_refused(libaf):

@@ -90,3 +90,14 @@ def test_rollout_gradient_matches_central_differences(fake, n_steps, every):
         x = _map(x, dt)
     for got, want in zip(fake.calls, reversed(states)):
         assert torch.equal(got, want)
+
+
+def test_second_backward_raises_a_clear_error(fake):
+    """The first backward releases the solver and the checkpoints."""
+    grid = I.Grid(3, 2, 0.0, 0.0, 0.1)
+    x0 = torch.from_numpy(_rng.normal(size=SHAPE)).requires_grad_(True)
+    xn = AG.rollout(x0, grid, 1.4, 0.3, 4, 2)
+    J = (xn ** 2).sum()
+    J.backward(retain_graph=True)
+    with pytest.raises(RuntimeError, match="one backward pass"):
+        J.backward()

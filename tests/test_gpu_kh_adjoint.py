@@ -71,25 +71,53 @@ def _ke_gpu_fp64(P, x, n_steps):
     return _ke(y, P.grid.h)
 
 
-# The FP32 adjoint is linearised about the FP32 trajectory, which near the sheet
-# already departs from the FP64 one at 100 steps (the FP32 and FP64 gradients
-# differ there by up to 2e-3 of max |g|); the measured directional error is
-# 2e-5, hence 1e-4.  FP64: measured 1.1e-7.
+N_DIRECTIONS = 64  # the workload's seeded directions
+
+
+@pytest.fixture(scope="module")
+def kh_differences(kh_full):
+    """Central differences (FP64 GPU step, eps 1e-7) of J after LINEAR_STEPS
+    steps along N_DIRECTIONS seeded smooth directions: (directions, values)."""
+    P = kh_full
+    eps = 1e-7
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp64")
+
+    def J(x):
+        s.set_state(x)
+        s.step(P.dt, LINEAR_STEPS)
+        return _ke(s.state(), P.grid.h)
+
+    dirs, fds = [], []
+    for seed in range(2000, 2000 + N_DIRECTIONS):
+        d = I.smooth_direction(P.grid, seed)
+        dirs.append(seed)
+        fds.append((J(P.state + eps * d) - J(P.state - eps * d)) / (2 * eps))
+    s.close()
+    return dirs, fds
+
+
+# Each direction's error |adjoint - difference| is stated relative to the
+# largest |difference| over the directions: some seeded directions are nearly
+# orthogonal to the gradient, and their own difference is then too small to
+# normalise by.  The FP32 adjoint is linearised about the FP32 trajectory, which
+# near the sheet already departs from the FP64 one at 100 steps (the FP32 and
+# FP64 gradients differ there by up to 2e-3 of max |g|), hence 1e-4 for FP32;
+# FP64 1e-6.
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-6)])
-def test_kh_1024_gradient_matches_differences_in_linear_regime(kh_full, precision, tol):
+def test_kh_1024_gradient_matches_differences_in_linear_regime(kh_full, kh_differences,
+                                                               precision, tol):
     P = kh_full
     _, _, g = _rollout(P, LINEAR_STEPS, EVERY, precision)
-    eps = 1e-7
-    worst = 0.0
-    for seed in (2000, 2001, 2002):
-        d = I.smooth_direction(P.grid, seed)
-        fd = (_ke_gpu_fp64(P, P.state + eps * d, LINEAR_STEPS) -
-              _ke_gpu_fp64(P, P.state - eps * d, LINEAR_STEPS)) / (2 * eps)
-        ad = float(np.sum(g * d))
-        rel = abs(ad - fd) / abs(fd)
-        worst = max(worst, rel)
-        assert rel <= tol, (precision, seed, ad, fd, rel)
-    print(f"KH 1024^2, {LINEAR_STEPS} steps, {precision}: adjoint vs central differences {worst:.2e}")
+    seeds, fds = kh_differences
+    fds = np.array(fds)
+    ads = np.array([float(np.sum(g * I.smooth_direction(P.grid, seed))) for seed in seeds])
+    err = np.abs(ads - fds) / np.max(np.abs(fds))
+    own = np.abs(ads - fds) / np.abs(fds)
+    print(f"KH 1024^2, {LINEAR_STEPS} steps, {precision}, {len(seeds)} directions: adjoint vs "
+          f"central differences, max error / max |difference| {err.max():.2e}; relative to "
+          f"each direction's own difference: median {np.median(own):.2e}, max {own.max():.2e} "
+          f"(|difference| from {np.min(np.abs(fds)):.2e} to {np.max(np.abs(fds)):.2e})")
+    assert err.max() <= tol, err
 
 
 def test_kh_1024_full_rollout_gradient(kh_full):
@@ -135,24 +163,57 @@ def test_kh_32_copy_gradient_matches_oracle_differences(orc, kh_full, precision,
     print(f"KH 32^2 copy, {n_steps} steps, {precision}: adjoint vs oracle differences {worst:.2e}")
 
 
-def test_kh_1024_fp32_vs_fp64(kh_full):
-    """FP32 against FP64 on the workload's own (unperturbed) data.  The difference
-    sits on the rows of the two vortex sheets and grows there by about 12x every
-    50 steps from step 50 on (the growth the gradient shows): 3.5e-6 after 50
-    steps, 4.0e-5 (FP32) and 2.8e-5 (FP32 compensated) after 100 in the
-    per-field form.  Away from the sheets (more than 48 rows) it stays at the
-    level of the smooth workloads."""
+def _rel_per_plane(a, b):
+    num = np.max(np.abs(a - b), axis=(1, 2))
+    den = np.maximum(np.max(np.abs(b), axis=(1, 2)), 1e-300)
+    return float(np.max(num / den))
+
+
+def _fp64_run(P, x0):
+    s = af.Solver(P.grid, P.gamma, x0, precision="fp64")
+    s.step(P.dt, 50)
+    y50 = s.state()
+    s.step(P.dt, 50)
+    y100 = s.state()
+    s.close()
+    return y50, y100
+
+
+def test_kh_1024_fp32_vs_fp64_against_its_conditioning():
+    """FP32 against FP64 on the workload's own (unperturbed) data, next to the
+    workload's conditioning: FP64 from initial data perturbed at the FP32
+    rounding level, (a) every value multiplied by 1 + 2^-24 r with r seeded
+    uniform in [-1, 1], (b) every value rounded to float32 and back, against
+    FP64 from the exact data.  The distances are stated in both norms (per
+    plane, and per field with velocity and momentum as vectors).
+
+    The difference sits on the rows of the two vortex sheets and grows there
+    about 12x every 50 steps from step 50 on, for the FP32 modes and for the
+    perturbed FP64 runs alike: the grid-scale Kelvin-Helmholtz growth of the
+    unresolved sheets amplifies any perturbation at rounding level.  FP32
+    rounds its stored state at every step, not once, so its difference is a
+    small multiple of that of one perturbation of the initial data.  The test
+    asserts that multiple (at most 4 after 100 steps, in either norm) instead
+    of the fixed 2e-5 that the smooth workloads meet; away from the sheets
+    (more than 48 rows) and after 50 steps the 2e-5 bound holds as it is."""
     from bench import rel_linf_fields
     P = I.kelvin_helmholtz(n=N_FULL)
     sheet = np.minimum(np.abs(np.arange(N_FULL) - N_FULL // 4),
                        np.abs(np.arange(N_FULL) - 3 * N_FULL // 4))
     far = sheet > 48
-    s = af.Solver(P.grid, P.gamma, P.state, precision="fp64")
-    s.step(P.dt, 50)
-    b50 = s.state()
-    s.step(P.dt, 50)
-    b100 = s.state()
-    s.close()
+    b50, b100 = _fp64_run(P, P.state)
+    rng = np.random.default_rng(4242)
+    pert = {"relative 2^-24": P.state * (1.0 + 2.0 ** -24 * rng.uniform(-1, 1, P.state.shape)),
+            "float32 round trip": P.state.astype(np.float32).astype(np.float64)}
+    cond = {}
+    for name, x0 in pert.items():
+        c50, c100 = _fp64_run(P, x0)
+        cond[name] = (rel_linf_fields(c100, b100), _rel_per_plane(c100, b100))
+        print(f"KH 1024^2 fp64 ({name} perturbation) vs fp64: 50 steps "
+              f"{rel_linf_fields(c50, b50):.2e} / {_rel_per_plane(c50, b50):.2e}, 100 steps "
+              f"{cond[name][0]:.2e} / {cond[name][1]:.2e} (per field / per plane)")
+    ref_field = max(c[0] for c in cond.values())
+    ref_plane = max(c[1] for c in cond.values())
     for precision in ("fp32", "fp32_comp"):
         s = af.Solver(P.grid, P.gamma, P.state, precision=precision)
         s.step(P.dt, 50)
@@ -161,8 +222,11 @@ def test_kh_1024_fp32_vs_fp64(kh_full):
         a100 = s.state()
         s.close()
         e50, e100 = rel_linf_fields(a50, b50), rel_linf_fields(a100, b100)
+        p50, p100 = _rel_per_plane(a50, b50), _rel_per_plane(a100, b100)
         efar = rel_linf_fields(a100[:, far], b100[:, far])
-        print(f"KH 1024^2 {precision} vs fp64 (per field): 50 steps {e50:.2e}, "
-              f"100 steps {e100:.2e}, 100 steps away from the sheets {efar:.2e}")
+        print(f"KH 1024^2 {precision} vs fp64: 50 steps {e50:.2e} / {p50:.2e}, 100 steps "
+              f"{e100:.2e} / {p100:.2e} (per field / per plane), 100 steps away from the "
+              f"sheets {efar:.2e}; ratio to the rounding-level perturbation "
+              f"{e100 / ref_field:.2f} / {p100 / ref_plane:.2f}")
         assert e50 < 2e-5 and efar < 2e-5
-        assert e100 < 1e-4
+        assert e100 <= 4 * ref_field and p100 <= 4 * ref_plane

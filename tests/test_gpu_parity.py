@@ -66,6 +66,32 @@ def test_fp64_matches_oracle_vortex_100_steps(orc):
     assert err < TOL64
 
 
+def test_vortex_against_the_exact_translate():
+    """Isentropic vortex (Sec. 6.2) on the GPU against its exact solution, the
+    initial vortex translated by the free stream, after 100 steps of the 32^2
+    workload (t = 3.75) and at the same time on 64^2 (200 steps).  The
+    oracle's errors on the same runs are 8.8e-3 (32^2) and 1.3e-3 (64^2) in the
+    density average against a vortex depth of 0.48 (log2 ratio 2.8), and at
+    most 2.3% of a plane's range on any plane at 32^2.  The tails of the vortex are not periodic on [-5,5]^2,
+    which puts a floor near 1e-5 far below these errors."""
+    P = I.vortex(n=32)
+    T = 100 * P.dt
+    errs = {}
+    for n in (32, 64):
+        Q = I.vortex(n=n)
+        ns = int(round(T / Q.dt))
+        got = run_gpu(Q, ns, "fp64", dt=T / ns)
+        ex = I.vortex_exact(Q.grid, T)
+        # per plane: max |error| over the plane's range of values
+        errs[n] = np.max(np.abs(got - ex), axis=(1, 2)) / np.ptp(ex, axis=(1, 2))
+        print("vortex %d^2 vs exact after t = %.3f: per plane max |error| / range %s"
+              % (n, T, np.array2string(errs[n], precision=2)))
+    assert np.max(errs[32]) < 3e-2, errs[32]  # oracle: 2.3e-2 at most
+    order = np.log2(errs[32][0] / errs[64][0])
+    print("density-average order 32 -> 64: %.2f" % order)
+    assert order > 2.3, order
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
 def test_fp32_vs_fp64_vortex_100_steps(precision):
     P = I.vortex(n=32)
@@ -228,6 +254,31 @@ def test_errors_are_reported():
     assert af.af_sync(s.handle) == af.AF_ERR_NONPHYSICAL
     s.close()
     assert af.af_step(0, 0.1, 1) == af.AF_ERR_ARG
+
+
+def test_timed_out_wait_is_reported_and_the_handle_recovers(monkeypatch):
+    """The bounded wait for a tile's tensor copies.  AF_TEST_LATE_WAIT=1 makes the
+    first such wait of every CTA of the handle's first step give up at once (the
+    copies are real and complete; the CTA drains them, flags the timeout and
+    stops).  100 x 70 cells: 12 tiles, two of them staged by tensor copies.  The
+    step must report AF_ERR_TIMEOUT, keep reporting it until the state is reset,
+    and the next step after af_set_state must be bitwise the plain step."""
+    P = I.random_smooth(100, 70, seed=5, amp=0.05)
+    clean = af.Solver(P.grid, P.gamma, P.state, precision="fp32_comp")
+    clean.step(P.dt, 1)
+    want = clean.state()
+    clean.close()
+    monkeypatch.setenv("AF_TEST_LATE_WAIT", "1")
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp32_comp")
+    monkeypatch.delenv("AF_TEST_LATE_WAIT")
+    assert af.af_step(s.handle, P.dt, 1) == af.AF_OK  # asynchronous
+    assert af.af_sync(s.handle) == af.AF_ERR_TIMEOUT
+    assert af.af_step(s.handle, P.dt, 1) == af.AF_ERR_TIMEOUT  # latched
+    s.set_state(P.state)  # clears the latch
+    s.step(P.dt, 1)
+    s.sync()
+    assert np.array_equal(s.state(), want)
+    s.close()
 
 
 def test_device_tensors_and_stream():

@@ -81,3 +81,45 @@ def test_noalloc_rejects_grids_beyond_its_work_area():
     rc = step_noalloc(ctypes.byref(g), 1.4, 1e-3, af.AF_TAI, ctypes.byref(st), ctypes.byref(st),
                       None)
     assert rc == af.AF_ERR_ARG
+
+
+def test_noalloc_clears_a_flag_left_by_the_previous_call():
+    """The work area keeps the last call's contents, its error word included.  A
+    call whose time step is far above the acoustic CFL limit raises the
+    device-side CFL flag (reported, not faulted); the next, valid call on the
+    same stream must start from a clear error word and match the handle step."""
+    torch = pytest.importorskip("torch")
+    step_noalloc = _lib()
+    P = I.random_smooth(16, 16, seed=1)
+    n = P.grid.nx * P.grid.ny
+    g = af.AfGrid(P.grid.nx, P.grid.ny, P.grid.h)
+    s = af.Solver(P.grid, P.gamma, P.state, precision="fp64")
+    s.step(P.dt, 1)
+    want = s.state()
+    s.close()
+    a = torch.from_numpy(P.state).cuda()
+    b = torch.empty_like(a)
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    rc = step_noalloc(ctypes.byref(g), P.gamma, 3.0 * P.dt, af.AF_TAI, ctypes.byref(_state(a, n)),
+                      ctypes.byref(_state(b, n)), ctypes.c_void_p(stream))
+    assert rc == af.AF_ERR_CFL
+    rc = step_noalloc(ctypes.byref(g), P.gamma, P.dt, af.AF_TAI, ctypes.byref(_state(a, n)),
+                      ctypes.byref(_state(b, n)), ctypes.c_void_p(stream))
+    assert rc == af.AF_OK
+    assert rel_linf(b.cpu().numpy(), want) < TOL64
+
+
+def test_noalloc_rejects_overlapping_input_and_output():
+    """`out` is written while later kernels of the step still read `in`."""
+    torch = pytest.importorskip("torch")
+    step_noalloc = _lib()
+    nx = ny = 16
+    g = af.AfGrid(nx, ny, 0.1)
+    a = torch.ones((16, ny, nx), dtype=torch.float64, device="cuda")
+    same = af._state_struct(a.data_ptr(), nx * ny)
+    shifted = af._state_struct(a.data_ptr() + 8 * nx * ny, nx * ny)  # planes shifted by one
+    for out in (same, shifted):
+        rc = step_noalloc(ctypes.byref(g), 1.4, 1e-3, af.AF_TAI, ctypes.byref(same),
+                          ctypes.byref(out), None)
+        assert rc == af.AF_ERR_ARG
