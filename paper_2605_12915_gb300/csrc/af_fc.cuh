@@ -166,9 +166,12 @@ __device__ void arc_table(double phi, double T[NM][NM]) {
   T[1][0] = s;
   T[0][1] = 1.0 - c;
   T[1][1] = 0.5 * s * s;
+  // reduce the sine power while it is at least 2, else the cosine power (then
+  // i >= 2, since n >= 2 and (1, 1) is a base case)
   for (int n = 2; n < NM; ++n)
     for (int i = 0; i <= n; ++i) {
       const int j = n - i;
+      if (i == 1 && j == 1) continue;
       if (j >= 2)
         T[i][j] = (-ipow(s, j - 1) * ipow(c, i + 1) + (j - 1) * T[i][j - 2]) / n;
       else
