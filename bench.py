@@ -25,6 +25,8 @@ shear2000  the workload at its stated length, 2000 steps: throughput, drift of
 ensemble   the 256-grid vortex ensemble, one batched launch per step against
            per-grid launches.
 adjoint    the discrete adjoint step against the forward step.
+foot_centred  context: the FP64 step with the foot-centred point update
+           against the FP64 transported step on a 128^2 copy.
 cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload.
 --impl reference  times the oracle itself (this workload has no other
            reference implementation), on rank 0 only.
@@ -65,6 +67,8 @@ def parse():
     p.add_argument("--shear-steps", type=int, default=2000,
                    help="steps of the full-length shear-layer run (conservation drift and "
                         "entropy; 0: skip)")
+    p.add_argument("--no-fc", action="store_true",
+                   help="skip the cost of the foot-centred variant (context)")
     p.add_argument("--fp32-steps", type=int, default=200,
                    help="steps of the plain FP32 (uncompensated) leg (0: skip)")
     p.add_argument("--adjoint-steps", type=int, default=5,
@@ -477,6 +481,7 @@ def main():
         if args.shear_steps > 0 and extras else None
     fp32_plain = plain_fp32_leg(af, P, args.fp32_steps, stream, torch, alu_peak, hbm) \
         if args.fp32_steps > 0 and extras and args.precision == "fp32_comp" else None
+    foot_centred = foot_centred_cost(af, I, stream, torch) if extras and not args.no_fc else None
     drift = (inv1[:4] - inv0[:4]) / np.array([inv0[0], inv0[0], inv0[0], inv0[3]])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -496,6 +501,7 @@ def main():
             "adjoint": adjoint,
             "ensemble": ensemble,
             "fp32_plain": fp32_plain,
+            "foot_centred": foot_centred,
             "shear2000": shear_long,
             "conservation_drift": [float(x) for x in drift],
             "entropy_change": float(inv1[4] - inv0[4])}
@@ -585,6 +591,28 @@ def shear_long_run(af, P, steps, stream, torch, local, uuid):
             "kinetic_energy": {"initial": float(inv0[6]), "final": float(inv1[6])},
             "min_rho": float(inv1[8]), "min_p": float(inv1[9]),
             "clocks": clk.summary()}
+
+
+def foot_centred_cost(af, I, stream, torch, n=128, steps=3):
+    """Context, not a target: the FP64 step with the foot-centred point update
+    (Appendix C) against the FP64 transported step, same shear layer at n^2."""
+    P = I.shear(n=n)
+    out = {"n": n, "steps": steps}
+    for variant in ("fc", "tai"):
+        s = af.Solver(P.grid, P.gamma, P.state, precision="fp64", variant=variant, stream=stream)
+        s.step(P.dt, 1)
+        s.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(P.dt, steps)
+        e1.record(stream)
+        e1.synchronize()
+        s.sync()
+        s.close()
+        out[variant + "_fp64_ms_per_step"] = e0.elapsed_time(e1) / steps
+    out["cost_ratio"] = out["fc_fp64_ms_per_step"] / out["tai_fp64_ms_per_step"]
+    return out
 
 
 def plain_fp32_leg(af, P, steps, stream, torch, alu_peak, hbm):

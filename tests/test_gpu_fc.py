@@ -60,9 +60,11 @@ def test_fc_vortex_matches_oracle(orc):
 
 
 def test_fc_at_rest_is_the_transported_step():
+    """A pulse at rest: in its first step every foot is its point, so the
+    foot-centred step is the transported one (later steps move the fluid)."""
     P = I.pulse(n=40, amp=0.1, width2=0.05)
-    a = run_gpu(P, 3, "fc")
-    b = run_gpu(P, 3, "tai")
+    a = run_gpu(P, 1, "fc")
+    b = run_gpu(P, 1, "tai")
     assert rel_linf(a, b) < 1e-13
 
 
