@@ -749,11 +749,11 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
       float dx3[3], dy3[3], dx31[3], dy31[3];
       {
         const float fx = fmaf(0.5f, (float)ox, dfx), fy = fmaf(0.5f, (float)oy, dfy);
-        lagrange3_d(2.f * (fx - floorf(fx)) - 1.f, dx3);
-        lagrange3_d(2.f * (fy - floorf(fy)) - 1.f, dy3);
+        lagrange3_d(fmaf(2.f, fx - floorf(fx), -1.f), dx3);
+        lagrange3_d(fmaf(2.f, fy - floorf(fy), -1.f), dy3);
         const float gx = fmaf(0.5f, (float)ox, d1x), gy = fmaf(0.5f, (float)oy, d1y);
-        lagrange3_d(2.f * (gx - floorf(gx)) - 1.f, dx31);
-        lagrange3_d(2.f * (gy - floorf(gy)) - 1.f, dy31);
+        lagrange3_d(fmaf(2.f, gx - floorf(gx), -1.f), dx31);
+        lagrange3_d(fmaf(2.f, gy - floorf(gy), -1.f), dy31);
       }
       const int dcf = (py + 1 + iy) * DCW + (px + 1 + ix);  // D cell of the foot cell
       float lwf[4], ld[3];  // adjoints of W at the foot and of the interpolated increments
@@ -783,7 +783,7 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
         lpP += -ly[0] * d2 * rp * igp * ipp;
         ld[0] = ld[1] = ld[2] = 0.f;
       }
-      // adjoint of the foot's local coordinates.  D holds (u + du, v + dv, dp);
+      // adjoint of the foot's local coordinates.  D holds (u + du, v + dv) and dp;
       // u and du enter the transported update with the same weight.
       float lxi = 0.f, leta = 0.f;
 #pragma unroll
@@ -794,8 +794,8 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
           float dot;
           if (a.variant == 0) {
             const int dn = dcf + (b >> 1) * DCW + (q >> 1);
-            dot = n[m].x * lwf[0] + Ds[(fn * 3) * DPL + dn] * lwf[1] +
-                  Ds[(fn * 3 + 1) * DPL + dn] * lwf[2] + n[m].w * lwf[3] +
+            const float2 uv = reinterpret_cast<const float2*>(Ds + fn * 3 * DPL)[dn];
+            dot = n[m].x * lwf[0] + uv.x * lwf[1] + uv.y * lwf[2] + n[m].w * lwf[3] +
                   Ds[(fn * 3 + 2) * DPL + dn] * ld[2];
           } else {
             dot = n[m].x * lwf[0] + n[m].y * lwf[1] + n[m].z * lwf[2] + n[m].w * lwf[3];

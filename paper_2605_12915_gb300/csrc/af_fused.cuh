@@ -80,8 +80,8 @@ struct FusedGeom {
 };
 
 // W plane of family f: W + f WPL (float4 per node: rho~, u, v, p~).
-// D plane of (duration s, family f, component k): D + ((4 s + f) 3 + k) DPL,
-// k = du, dv, dp.  After phase 3 the points of duration s of family f live at
+// D block of (duration s, family f) at D + (4 s + f) 3 DPL: a float2 plane of
+// (u + du, v + dv) (2 DPL floats), then a float plane of dp (DPL floats).  After phase 3 the points of duration s of family f live at
 // PT(s) + f PPL (float4), PT(s) = the start of D(s).  During phases 0-1 the
 // averages (and lo words) of the W cells occupy D as 8 planes of WPL floats.
 
@@ -139,12 +139,34 @@ __device__ __forceinline__ float q2_eval(const float* pV, const float* pEv, cons
   return fmaf(ly[0], r0, fmaf(ly[1], r1, ly[2] * r2));
 }
 
+// the same for a pair of fields held as float2 planes (one load per node)
+template <int R>
+__device__ __forceinline__ float2 q2_eval2(const float2* pV, const float2* pEv, const float2* pEh,
+                                           const float2* pC, int c, const float lx[3],
+                                           const float ly[3]) {
+  const float2 a0 = pV[c], a1 = pEh[c], a2 = pV[c + 1];
+  const float2 b0 = pEv[c], b1 = pC[c], b2 = pEv[c + 1];
+  const float2 c0 = pV[c + R], c1 = pEh[c + R], c2 = pV[c + R + 1];
+  float2 o;
+  o.x = fmaf(ly[0], fmaf(lx[0], a0.x, fmaf(lx[1], a1.x, lx[2] * a2.x)),
+             fmaf(ly[1], fmaf(lx[0], b0.x, fmaf(lx[1], b1.x, lx[2] * b2.x)),
+                  ly[2] * fmaf(lx[0], c0.x, fmaf(lx[1], c1.x, lx[2] * c2.x))));
+  o.y = fmaf(ly[0], fmaf(lx[0], a0.y, fmaf(lx[1], a1.y, lx[2] * a2.y)),
+             fmaf(ly[1], fmaf(lx[0], b0.y, fmaf(lx[1], b1.y, lx[2] * b2.y)),
+                  ly[2] * fmaf(lx[0], c0.y, fmaf(lx[1], c1.y, lx[2] * c2.y))));
+  return o;
+}
+
 // local coordinates of a point displaced by d (cells) from lattice offset o (0
 // or 1 half cell): cell offset (floor) and Lagrange weights.
 __device__ __forceinline__ int foot_axis(int o, float d, float l[3]) {
   const float f = fmaf(0.5f, (float)o, d);
   const float fl = floorf(f);
-  lagrange3(2.f * (f - fl) - 1.f, l);
+  // the Q2 Lagrange basis at t = 2 (f - fl) - 1, its products as multiply-adds
+  const float t = fmaf(2.f, f - fl, -1.f), ht = 0.5f * t;
+  l[0] = fmaf(ht, t, -ht);
+  l[1] = fmaf(-t, t, 1.f);
+  l[2] = fmaf(ht, t, ht);
   return (int)fl;
 }
 
@@ -580,22 +602,22 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
         d[1] = r * fmaf(r, fmaf(r, fmaf(r, cv[3], cv[2]), cv[1]), cv[0]);
       };
       float d[3];
-      float* D0 = D + fam * 3 * DPL + dc;
-      float* D1 = D + (4 + fam) * 3 * DPL + dc;
+      float2* D0 = reinterpret_cast<float2*>(D + fam * 3 * DPL) + dc;
+      float2* D1 = reinterpret_cast<float2*>(D + (4 + fam) * 3 * DPL) + dc;
+      float* D0p = D + fam * 3 * DPL + 2 * DPL + dc;
+      float* D1p = D + (4 + fam) * 3 * DPL + 2 * DPL + dc;
       // owned node (for the stored intermediates)
       const int gi = i0 - 1 + dx, gj = j0 - 1 + dy;
       const bool own = INTER && dx >= 1 && dx <= TX && dy >= 1 && dy <= TY && gi < nx && gj < ny;
       const size_t gid = own ? (size_t)gj * nx + gi : 0;
       horner(0.5f * r1, d);
-      D0[0] = wk.y + d[0];
-      D0[DPL] = wk.z + d[1];
-      D0[2 * DPL] = d[2];
+      *D0 = make_float2(wk.y + d[0], wk.z + d[1]);
+      *D0p = d[2];
       if (own)
         for (int k = 0; k < 3; ++k) a.inc[0][fam][k][gid] = d[k];
       horner(r1, d);
-      D1[0] = wk.y + d[0];
-      D1[DPL] = wk.z + d[1];
-      D1[2 * DPL] = d[2];
+      *D1 = make_float2(wk.y + d[0], wk.z + d[1]);
+      *D1p = d[2];
       if (own)
         for (int k = 0; k < 3; ++k) a.inc[1][fam][k][gid] = d[k];
     }
@@ -646,10 +668,16 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
         // u_f + du_f = I_h(u + du)(P_f) since both interpolants share the basis
         const int dcf = (py + 1 + iy) * DCW + (px + 1 + ix);  // D cell of the foot cell
         float e[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          e[q] = q2_eval<DCW>(Ds + (0 * 3 + q) * DPL, Ds + (1 * 3 + q) * DPL,
-                              Ds + (2 * 3 + q) * DPL, Ds + (3 * 3 + q) * DPL, dcf, lx, ly);
+        {
+          const float2 e01 = q2_eval2<DCW>(reinterpret_cast<const float2*>(Ds),
+                                           reinterpret_cast<const float2*>(Ds + 3 * DPL),
+                                           reinterpret_cast<const float2*>(Ds + 6 * DPL),
+                                           reinterpret_cast<const float2*>(Ds + 9 * DPL), dcf, lx,
+                                           ly);
+          e[0] = e01.x;
+          e[1] = e01.y;
+        }
+        e[2] = q2_eval<DCW>(Ds + 2 * DPL, Ds + 5 * DPL, Ds + 8 * DPL, Ds + 11 * DPL, dcf, lx, ly);
         const float rf = gas.rho_ref + rft, pf = gas.p_ref + pft;
         if (!(rf > 0.f && pf > 0.f)) bad |= FLAG_NONPHYSICAL;
         nw.r = rft + __fdividef(e[2] * rf, gas.gamma * pf);
@@ -659,8 +687,9 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       } else {
         // additive update (Eq. barsukow-additive), acoustic rho closure at P
         const int dcp = (py + 1) * DCW + (px + 1);
-        const float du = Ds[(fam * 3 + 0) * DPL + dcp] - wp.y;
-        const float dv = Ds[(fam * 3 + 1) * DPL + dcp] - wp.z;
+        const float2 uv = reinterpret_cast<const float2*>(Ds + fam * 3 * DPL)[dcp];
+        const float du = uv.x - wp.y;
+        const float dv = uv.y - wp.z;
         const float dp = Ds[(fam * 3 + 2) * DPL + dcp];
         nw.r = rft + __fdividef(dp * (gas.rho_ref + wp.x), gas.gamma * (gas.p_ref + wp.w));
         nw.u = AF_Q2(n, y, lx, ly) + du;
