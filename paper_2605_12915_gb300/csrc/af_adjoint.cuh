@@ -581,8 +581,15 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
   acc.node(FAM, i, j, lrho, luK, lvK, lp + lpK);
 }
 
+// resident 256-thread blocks per SM requested of the acoustic and centre
+// adjoints (their register budget follows; they wait on scattered loads)
+#ifndef AF_ADJ_NODE_MINB
+#define AF_ADJ_NODE_MINB 3
+#endif
+
 template <int FAM, typename T>
-__global__ void k_adj_acoustic(const __grid_constant__ AdjView<T> v) {
+__global__ void __launch_bounds__(256, AF_ADJ_NODE_MINB)
+    k_adj_acoustic(const __grid_constant__ AdjView<T> v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i < v.nx && j < v.ny) acoustic_adj<FAM>(v, vec_adj(v), i, j);
 }
@@ -591,7 +598,8 @@ __global__ void k_adj_acoustic(const __grid_constant__ AdjView<T> v) {
 // Centre recovery (Eq. center-node), reversed.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_adj_center(const __grid_constant__ AdjView<T> v) {
+__global__ void __launch_bounds__(256, AF_ADJ_NODE_MINB)
+    k_adj_center(const __grid_constant__ AdjView<T> v) {
   const VecAdj<T> acc = vec_adj(v);
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const size_t ps = v.ps;
