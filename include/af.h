@@ -41,8 +41,11 @@ typedef enum {
   AF_ERR_NONPHYSICAL = 5, /* rho <= 0 or p <= 0 where a sound speed is needed */
   AF_ERR_NONFINITE = 6,   /* NaN or Inf produced */
   AF_ERR_STATE = 7,       /* handle unusable (a previous CUDA error) */
-  AF_ERR_TIMEOUT = 8      /* a kernel's bounded wait for its own asynchronous copies ran
+  AF_ERR_TIMEOUT = 8,     /* a kernel's bounded wait for its own asynchronous copies ran
                              out; the kernel stopped early and the step's result is invalid */
+  AF_ERR_BOUNDS = 9       /* debug builds only (compiled with AF_BOUNDS_CHECK): a checked
+                             shared-memory index of the fused step left its region; the
+                             access used a valid index instead and the result is invalid */
 } af_status;
 
 typedef enum {

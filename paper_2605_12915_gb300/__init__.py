@@ -16,7 +16,7 @@ import os
 from . import _build
 
 AF_OK, AF_ERR_ARG, AF_ERR_CUDA, AF_ERR_ALLOC, AF_ERR_CFL, AF_ERR_NONPHYSICAL, \
-    AF_ERR_NONFINITE, AF_ERR_STATE, AF_ERR_TIMEOUT = range(9)
+    AF_ERR_NONFINITE, AF_ERR_STATE, AF_ERR_TIMEOUT, AF_ERR_BOUNDS = range(10)
 AF_FP64, AF_FP32, AF_FP32_COMP = 0, 1, 2
 AF_TAI, AF_RB, AF_FC = 0, 1, 2
 AF_HOST, AF_DEVICE = 0, 1

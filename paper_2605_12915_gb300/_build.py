@@ -25,13 +25,15 @@ def nvcc():
     return "nvcc"
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile csrc/af_api.cu into paper_2605_12915_gb300/libaf.so.  Rebuilds when
-    a source is newer than the library."""
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build(force=False, verbose=False, extra_flags=(), out=None):
+    """Compile the CUDA sources into paper_2605_12915_gb300/libaf.so (or `out`,
+    e.g. a debug variant built with extra_flags).  Rebuilds when a source is
+    newer than the library."""
+    lib = out or LIB
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(d) <= t for d in _deps()):
-            return LIB
+            return lib
     # -fmad=false: no implicit multiply-add contraction.  Every value that two
     # CTAs compute redundantly (tile-boundary points and edge fluxes) must round
     # identically in every unrolled copy of the code, or conservation breaks;
@@ -41,7 +43,8 @@ def build(force=False, verbose=False, extra_flags=()):
     # one object per translation unit, compiled in parallel, then one link
     objs, procs = [], []
     for src in SOURCES:
-        obj = os.path.join(CSRC, "_build", src.replace(".cu", ".o"))
+        tag = os.path.splitext(os.path.basename(lib))[0]
+        obj = os.path.join(CSRC, "_build", tag, src.replace(".cu", ".o"))
         os.makedirs(os.path.dirname(obj), exist_ok=True)
         cmd = [nvcc(), *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
@@ -51,9 +54,9 @@ def build(force=False, verbose=False, extra_flags=()):
     failed = [p.args for p in procs if p.wait() != 0]
     if failed:
         raise subprocess.CalledProcessError(1, failed[0])
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd, cwd=CSRC)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib

@@ -80,6 +80,7 @@ struct NvtxRange {
 };
 
 af_status map_flags(unsigned f) {
+  if (f & FLAG_BOUNDS) return AF_ERR_BOUNDS;
   if (f & FLAG_TIMEOUT) return AF_ERR_TIMEOUT;
   if (f & FLAG_NONPHYSICAL) return AF_ERR_NONPHYSICAL;
   if (f & FLAG_NONFINITE) return AF_ERR_NONFINITE;
@@ -511,6 +512,7 @@ const char* af_status_string(af_status s) {
     case AF_ERR_NONFINITE: return "non-finite value in the state";
     case AF_ERR_STATE: return "handle unusable after a CUDA error";
     case AF_ERR_TIMEOUT: return "a device-side wait for asynchronous copies timed out";
+    case AF_ERR_BOUNDS: return "a checked kernel index left its region (bounds-checking build)";
   }
   return "unknown status";
 }

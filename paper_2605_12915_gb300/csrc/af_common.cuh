@@ -14,7 +14,8 @@ enum : unsigned {
   FLAG_NONPHYSICAL = 2u,  // rho <= 0 or p <= 0 where c is needed
   FLAG_NONFINITE = 4u,    // NaN / Inf in the new state
   FLAG_REACH = 8u,        // convective foot more than one cell from its point
-  FLAG_TIMEOUT = 16u      // a bounded wait for the CTA's own asynchronous copies ran out
+  FLAG_TIMEOUT = 16u,     // a bounded wait for the CTA's own asynchronous copies ran out
+  FLAG_BOUNDS = 32u       // debug builds (AF_BOUNDS_CHECK): a checked index left its region
 };
 
 template <typename T>

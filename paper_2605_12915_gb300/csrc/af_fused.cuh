@@ -103,6 +103,24 @@ struct LoadW {
 
 __device__ __forceinline__ float clamp1(float d) { return fmaxf(fminf(d, 1.0f), -1.0f); }
 
+// Bounds-checking debug builds (-DAF_BOUNDS_CHECK): the shared-memory indices
+// of the fused step (foot cells, stencil and node cells, point, edge and flux
+// indices) are checked against [lo, hi) of their region; an index outside
+// raises FLAG_BOUNDS (AF_ERR_BOUNDS) and is replaced by lo, so the access stays
+// inside and the step completes.  Without the define the check compiles away.
+__device__ __forceinline__ int idx_checked(int i, int lo, int hi, unsigned& bad) {
+  if (i < lo || i >= hi) {
+    bad |= FLAG_BOUNDS;
+    return lo;
+  }
+  return i;
+}
+#ifdef AF_BOUNDS_CHECK
+#define AF_IDX(i, lo, hi) ::af::idx_checked((i), (lo), (hi), bad)
+#else
+#define AF_IDX(i, lo, hi) (i)
+#endif
+
 __device__ __forceinline__ Prim<float> prim4(float4 w) {
   Prim<float> p = {w.x, w.y, w.z, w.w};
   return p;
@@ -444,8 +462,8 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     for (int t = threadIdx.x; t < CW * CH; t += NT) {
       int cx, cy;
       chunked_xy<CW, CH>(t, cx, cy);
-      const float* S = D + cy * G::SW + cx + 2;
-      const int w = cy * CW + cx;
+      const float* S = D + AF_IDX(cy * G::SW + cx + 2, 0, G::SPL);
+      const int w = AF_IDX(cy * CW + cx, 0, WPL);
 #pragma unroll
       for (int f = 0; f < 3; ++f)
         W[f * WPL + w] = make_float4(S[(4 * f) * G::SPL], S[(4 * f + 1) * G::SPL],
@@ -514,7 +532,8 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
   for (int t = threadIdx.x; t < (CW - 1) * (CH - 1); t += NT) {
     int cx, cy;
     chunked_xy<CW - 1, CH - 1>(t, cx, cy);
-    const int c = cy * CW + cx, ca = AB + cy * ARS + cx + AOF;
+    const int c = AF_IDX(cy * CW + cx, 0, WPL - CW - 1);
+    const int ca = AF_IDX(AB + cy * ARS + cx + AOF, AB, AB + APL);
     float ub[4], lo[4], sc[4] = {0.f, 0.f, 0.f, 0.f}, se[4] = {0.f, 0.f, 0.f, 0.f}, uc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -561,7 +580,9 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     for (int t = threadIdx.x; t < nV + nEv + nEh + nC; t += NT) {
       int fam, dx, dy;
       acoustic_item<TX, TY>(t, fam, dx, dy);
-      const int wc = (dy + 1) * CW + (dx + 1), dc = dy * DCW + dx;
+      // (the stencils reach one cell around wc in every family plane)
+      const int wc = AF_IDX((dy + 1) * CW + (dx + 1), CW + 1, WPL - CW - 1);
+      const int dc = AF_IDX(dy * DCW + dx, 0, DPL);
       const float4 wk = W[fam * WPL + wc];
       const float rk = gas.rho_ref + wk.x, pk = gas.p_ref + wk.w;
       if (!(rk > 0.f && pk > 0.f)) bad |= FLAG_NONPHYSICAL;
@@ -643,14 +664,15 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       int fam, px, py;
       point_item<PW, G::PH>(t, fam, px, py);
       const int ox = fam == 2 ? 1 : 0, oy = fam == 1 ? 1 : 0;
-      const int wcP = (py + 2) * CW + (px + 2);  // W cell of the point's cell
+      const int wcP = AF_IDX((py + 2) * CW + (px + 2), 0, WPL);  // W cell of the point's cell
       const float4 wp = W[fam * WPL + wcP];
       // first Picard stage from the point's own velocity (Eq. adv-footpoint)
       const float d1x = -th * wp.y, d1y = -th * wp.z;
       if (!(fabsf(d1x) <= 1.f && fabsf(d1y) <= 1.f)) bad |= FLAG_REACH;
       float lx[3], ly[3];
       int ix = foot_axis(ox, clamp1(d1x), lx), iy = foot_axis(oy, clamp1(d1y), ly);
-      const int c1 = wcP + iy * CW + ix;
+      // (a cell's nine nodes reach one row and one column beyond it)
+      const int c1 = AF_IDX(wcP + iy * CW + ix, 0, WPL - CW - 1);
       float4 n[9];
       load_cell<CW, WPL>(W, c1, n);
       const float u1 = AF_Q2(n, y, lx, ly), v1 = AF_Q2(n, z, lx, ly);
@@ -659,14 +681,14 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       if (!(fabsf(dfx) <= 1.f && fabsf(dfy) <= 1.f)) bad |= FLAG_REACH;
       ix = foot_axis(ox, clamp1(dfx), lx);
       iy = foot_axis(oy, clamp1(dfy), ly);
-      const int c2 = wcP + iy * CW + ix;
+      const int c2 = AF_IDX(wcP + iy * CW + ix, 0, WPL - CW - 1);
       if (c2 != c1) load_cell<CW, WPL>(W, c2, n);
       const float rft = AF_Q2(n, x, lx, ly), pft = AF_Q2(n, w, lx, ly);  // rho~_f, p~_f
       Prim<float> nw;
       if (a.variant == 0) {
         // transported increment at the foot; rho from dp / c_f^2 (Sec. 6.1 step 4):
         // u_f + du_f = I_h(u + du)(P_f) since both interpolants share the basis
-        const int dcf = (py + 1 + iy) * DCW + (px + 1 + ix);  // D cell of the foot cell
+        const int dcf = AF_IDX((py + 1 + iy) * DCW + (px + 1 + ix), 0, DPL - DCW - 1);
         float e[3];
         {
           const float2 e01 = q2_eval2<DCW>(reinterpret_cast<const float2*>(Ds),
@@ -686,7 +708,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
         nw.p = pft + e[2];
       } else {
         // additive update (Eq. barsukow-additive), acoustic rho closure at P
-        const int dcp = (py + 1) * DCW + (px + 1);
+        const int dcp = AF_IDX((py + 1) * DCW + (px + 1), 0, DPL);
         const float2 uv = reinterpret_cast<const float2*>(Ds + fam * 3 * DPL)[dcp];
         const float du = uv.x - wp.y;
         const float dv = uv.y - wp.z;
@@ -725,7 +747,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
         if (k >= NPTS / NT && t >= NPTS) break;
         int fam, px, py;
         point_item<PW, G::PH>(t, fam, px, py);
-        P[fam * PPL + py * PW + px] = res[k];
+        P[AF_IDX(fam * PPL + py * PW + px, 0, 3 * PPL)] = res[k];
       }
     }
   }
@@ -768,9 +790,10 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     else
       chunked_xy<TX, G::PH>(t - NVE, ex, ey);
     const int fm = vert ? 1 : 2;              // E_v or E_h
-    const int wa = (ey + 2) * CW + (ex + 2);  // W cell of V(ex, ey)
+    const int wa = AF_IDX((ey + 2) * CW + (ex + 2), 0, WPL - CW);  // W cell of V(ex, ey)
     const int wb = vert ? wa + CW : wa + 1;   // the edge's other vertex
-    const int pa = ey * PW + ex, pb = vert ? pa + PW : pa + 1;
+    const int pa = AF_IDX(ey * PW + ex, 0, vert ? PPL - PW : PPL - 1);
+    const int pb = vert ? pa + PW : pa + 1;
     float F[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
@@ -827,6 +850,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       chunked_xy<TX, G::PH>(t - NVE, ex, ey);
       e = NVE + ey * TX + ex;
     }
+    e = AF_IDX(e, 0, NE);
 #pragma unroll
     for (int q = 0; q < 4; ++q) FLX[q * NE + e] = flux[k][q];
   }
@@ -838,8 +862,8 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     const int gi = i0 + cx, gj = j0 + cy;
     if (t >= TX * TY || gi >= nx || gj >= ny) continue;
     const size_t id = (size_t)gj * nx + gi;
-    const int fl = cy * PW + cx, fr = fl + 1;         // vertical edges x_i, x_{i+1}
-    const int gb = NVE + cy * TX + cx, gt = gb + TX;  // horizontal edges y_j, y_{j+1}
+    const int fl = AF_IDX(cy * PW + cx, 0, NVE - 1), fr = fl + 1;  // vertical edges x_i, x_{i+1}
+    const int gb = AF_IDX(NVE + cy * TX + cx, NVE, NE - TX), gt = gb + TX;  // horizontal y_j, y_{j+1}
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float* Fq = FLX + q * NE;

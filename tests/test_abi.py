@@ -44,9 +44,9 @@ def test_library_exports_every_declared_entry_point(libaf):
 
 def test_status_strings(libaf):
     libaf.af_status_string.restype = ctypes.c_char_p
-    for s in range(9):
+    for s in range(10):
         assert libaf.af_status_string(s) != b"unknown status"
-    assert libaf.af_status_string(9) == b"unknown status"
+    assert libaf.af_status_string(10) == b"unknown status"
 
 
 _BAD_INIT = {
@@ -92,6 +92,7 @@ def test_binding_constants_match_the_header():
     assert int(re.search(r"#define AF_BATCH_GEOMS (\d+)", text).group(1)) == af.AF_BATCH_GEOMS
     assert int(re.search(r"AF_NINV = (\d+)", text).group(1)) == af.AF_NINV
     assert int(re.search(r"AF_ERR_TIMEOUT = (\d+)", text).group(1)) == af.AF_ERR_TIMEOUT
+    assert int(re.search(r"AF_ERR_BOUNDS = (\d+)", text).group(1)) == af.AF_ERR_BOUNDS
     assert int(re.search(r"AF_FC = (\d+)", text).group(1)) == af.AF_FC
 
 

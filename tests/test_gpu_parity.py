@@ -56,6 +56,25 @@ def test_fp64_matches_oracle_random(orc, shape, variant):
     assert rel_linf(got, want) < TOL64
 
 
+@pytest.mark.parametrize("shape", [(3, 3), (4, 4), (5, 7)])
+def test_tiny_grids_match_oracle(orc, shape):
+    """Grids smaller than one tile and barely wider than the stencils' reach:
+    the periodic wrap is taken several times inside one tile.  FP64 with the
+    transported, additive and foot-centred point updates, and the fused FP32
+    kernels, 3 steps each, against the oracle on the same state."""
+    nx, ny = shape
+    P = I.random_smooth(nx, ny, seed=7 * nx + ny, amp=0.03)
+    runs = (("tai", 0, P.dt), ("rb", 1, 0.6 * P.dt), ("fc", 2, P.dt))
+    for variant, ov, dt in runs:
+        want = run_orc(orc, P, 3, ov, dt)
+        err = rel_linf(run_gpu(P, 3, "fp64", variant, dt), want)
+        assert err < TOL64, (shape, variant, err)
+        if variant == "tai":
+            for precision in ("fp32", "fp32_comp"):
+                err32 = rel_linf(run_gpu(P, 3, precision), want)
+                assert err32 < TOL32, (shape, precision, err32)
+
+
 def test_fp64_matches_oracle_vortex_100_steps(orc):
     """Isentropic vortex, 32^2, CFL 0.4, 100 steps, FP64, transported update."""
     P = I.vortex(n=32)
