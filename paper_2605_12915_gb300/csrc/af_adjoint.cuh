@@ -740,19 +740,20 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
 #pragma unroll
       for (int k = 0; k < 4; ++k) ly[k] = s == 0 ? lyh[k] : lyf[k];
       // forward: the two Picard stages as the fused step traces them
-      const float d1x = clamp1(-th * wp.y), d1y = clamp1(-th * wp.z);
+      // (shared node records are (u, v, rho~, p~))
+      const float d1x = clamp1(-th * wp.x), d1y = clamp1(-th * wp.y);
       float lx1[3], ly1[3];
       const int ix1 = foot_axis(ox, d1x, lx1), iy1 = foot_axis(oy, d1y, ly1);
       const int c1 = wcP + iy1 * CW + ix1;
       float4 n[9];
       load_cell<CW, WPL>(W, c1, n);
-      const float u1 = AF_Q2(n, y, lx1, ly1), v1 = AF_Q2(n, z, lx1, ly1);
+      const float u1 = AF_Q2(n, x, lx1, ly1), v1 = AF_Q2(n, y, lx1, ly1);
       const float dfx = clamp1(-th * u1), dfy = clamp1(-th * v1);
       float lx[3], lyb[3];
       const int ix = foot_axis(ox, dfx, lx), iy = foot_axis(oy, dfy, lyb);
       const int c2 = wcP + iy * CW + ix;
       if (c2 != c1) load_cell<CW, WPL>(W, c2, n);
-      const float rft = AF_Q2(n, x, lx, lyb), pft = AF_Q2(n, w, lx, lyb);
+      const float rft = AF_Q2(n, z, lx, lyb), pft = AF_Q2(n, w, lx, lyb);
       // local coordinates of the foot and of the first stage
       float dx3[3], dy3[3], dx31[3], dy31[3];
       {
@@ -781,7 +782,7 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
       } else {
         const int dcp = (py + 1) * DCW + (px + 1);
         const float d2 = Ds[(fam * 3 + 2) * DPL + dcp];
-        const float rp = gas.rho_ref + wp.x, pp = gas.p_ref + wp.w;
+        const float rp = gas.rho_ref + wp.z, pp = gas.p_ref + wp.w;
         const float igp = __fdividef(1.f, gas.gamma * pp), ipp = __fdividef(1.f, pp);
 #pragma unroll
         for (int k = 0; k < 4; ++k) lwf[k] = ly[k];
@@ -803,10 +804,10 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
           if (a.variant == 0) {
             const int dn = dcf + (b >> 1) * DCW + (q >> 1);
             const float2 uv = reinterpret_cast<const float2*>(Ds + fn * 3 * DPL)[dn];
-            dot = n[m].x * lwf[0] + uv.x * lwf[1] + uv.y * lwf[2] + n[m].w * lwf[3] +
+            dot = n[m].z * lwf[0] + uv.x * lwf[1] + uv.y * lwf[2] + n[m].w * lwf[3] +
                   Ds[(fn * 3 + 2) * DPL + dn] * ld[2];
           } else {
-            dot = n[m].x * lwf[0] + n[m].y * lwf[1] + n[m].z * lwf[2] + n[m].w * lwf[3];
+            dot = n[m].z * lwf[0] + n[m].x * lwf[1] + n[m].y * lwf[2] + n[m].w * lwf[3];
           }
           lxi += dx3[q] * lyb[b] * dot;
           leta += lx[q] * dy3[b] * dot;
@@ -821,7 +822,7 @@ __device__ __forceinline__ void tile_reverse(const StepArgs<float>& a, const Adj
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int m = 3 * b + q;
-          const float dot = n[m].y * lu1 + n[m].z * lv1;
+          const float dot = n[m].x * lu1 + n[m].y * lv1;
           lxi1 += dx31[q] * ly1[b] * dot;
           leta1 += lx1[q] * dy31[b] * dot;
         }

@@ -2,7 +2,7 @@
 //
 // Each CTA owns TX x TY cells.  Everything a step needs around them is staged
 // in shared memory, one plane per node family, indexed by cell:
-//   W   time-n values float4 (rho~, u, v, p~) of the vertex, x-edge, y-edge and
+//   W   time-n values float4 (u, v, rho~, p~) of the vertex, x-edge, y-edge and
 //       centre families of cells [i0-2, i0+TX+4) x [j0-2, j0+TY+4); the centre
 //       family is filled by this CTA's Simpson inversion (phase 1).
 //   D   acoustic increments (du, dv, dp) of every family for tau = dt/2 and
@@ -79,7 +79,7 @@ struct FusedGeom {
   static_assert(W_BYTES % 16 == 0 && DS_BYTES % 16 == 0, "float4 alignment");
 };
 
-// W plane of family f: W + f WPL (float4 per node: rho~, u, v, p~).
+// W plane of family f: W + f WPL (float4 per node: u, v, rho~, p~).
 // D block of (duration s, family f) at D + (4 s + f) 3 DPL: a float2 plane of
 // (u + du, v + dv) (2 DPL floats), then a float plane of dp (DPL floats).  After phase 3 the points of duration s of family f live at
 // PT(s) + f PPL (float4), PT(s) = the start of D(s).  During phases 0-1 the
@@ -96,7 +96,7 @@ struct LoadW {
     const int ax = ((F == 2 || F == 3) ? 1 : 0) + dx, by = ((F == 1 || F == 3) ? 1 : 0) + dy;
     const int fam = (ax & 1) ? ((by & 1) ? 3 : 2) : ((by & 1) ? 1 : 0);
     const float4 w = W[fam * WPL + cell + (by >> 1) * CW + (ax >> 1)];
-    PUV<float> o = {w.w, w.y, w.z};
+    PUV<float> o = {w.w, w.x, w.y};
     return o;
   }
 };
@@ -121,10 +121,21 @@ __device__ __forceinline__ int idx_checked(int i, int lo, int hi, unsigned& bad)
 #define AF_IDX(i, lo, hi) (i)
 #endif
 
+// Node records of the shared planes (W, and the points of each duration):
+// float4 (u, v, rho~, p~), so that (u, v) and (rho~, p~) each fill an aligned
+// register pair for the paired FP32 operations (__ffma2_rn, __fmul2_rn,
+// __fadd2_rn: two lanes in one instruction, each rounded as the scalar
+// operation, so a paired evaluation equals the scalar one bitwise).
+__device__ __forceinline__ float4 rec4(float r, float u, float v, float p) {
+  return make_float4(u, v, r, p);
+}
+__device__ __forceinline__ float2 rec_uv(const float4& q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 rec_rp(const float4& q) { return make_float2(q.z, q.w); }
 __device__ __forceinline__ Prim<float> prim4(float4 w) {
-  Prim<float> p = {w.x, w.y, w.z, w.w};
+  Prim<float> p = {w.z, w.x, w.y, w.w};
   return p;
 }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 // The nine W nodes of the cell at index c, ordered [b][a] (eta row, xi column).
 template <int CW, int WPL>
@@ -157,22 +168,46 @@ __device__ __forceinline__ float q2_eval(const float* pV, const float* pEv, cons
   return fmaf(ly[0], r0, fmaf(ly[1], r1, ly[2] * r2));
 }
 
+// sum_ab l_a(xi) l_b(eta) v_ab of a pair of fields (two lanes) over the nine
+// nodes v[] of a cell, ordered as load_cell; lxd, lyd hold each weight in both
+// lanes.  Each lane performs the operations of AF_Q2 in the same order.
+__device__ __forceinline__ float2 q2_pair(const float2 v[9], const float2 lxd[3],
+                                          const float2 lyd[3]) {
+  const float2 r0 = __ffma2_rn(lxd[0], v[0], __ffma2_rn(lxd[1], v[1], __fmul2_rn(lxd[2], v[2])));
+  const float2 r1 = __ffma2_rn(lxd[0], v[3], __ffma2_rn(lxd[1], v[4], __fmul2_rn(lxd[2], v[5])));
+  const float2 r2 = __ffma2_rn(lxd[0], v[6], __ffma2_rn(lxd[1], v[7], __fmul2_rn(lxd[2], v[8])));
+  return __ffma2_rn(lyd[0], r0, __ffma2_rn(lyd[1], r1, __fmul2_rn(lyd[2], r2)));
+}
+
+// the (u, v) and (rho~, p~) pairs of the nine node records n[] of a cell
+__device__ __forceinline__ float2 q2_uv(const float4 n[9], const float2 lxd[3],
+                                        const float2 lyd[3]) {
+  const float2 v[9] = {rec_uv(n[0]), rec_uv(n[1]), rec_uv(n[2]), rec_uv(n[3]), rec_uv(n[4]),
+                       rec_uv(n[5]), rec_uv(n[6]), rec_uv(n[7]), rec_uv(n[8])};
+  return q2_pair(v, lxd, lyd);
+}
+__device__ __forceinline__ float2 q2_rp(const float4 n[9], const float2 lxd[3],
+                                        const float2 lyd[3]) {
+  const float2 v[9] = {rec_rp(n[0]), rec_rp(n[1]), rec_rp(n[2]), rec_rp(n[3]), rec_rp(n[4]),
+                       rec_rp(n[5]), rec_rp(n[6]), rec_rp(n[7]), rec_rp(n[8])};
+  return q2_pair(v, lxd, lyd);
+}
+
 // the same for a pair of fields held as float2 planes (one load per node)
 template <int R>
 __device__ __forceinline__ float2 q2_eval2(const float2* pV, const float2* pEv, const float2* pEh,
-                                           const float2* pC, int c, const float lx[3],
-                                           const float ly[3]) {
-  const float2 a0 = pV[c], a1 = pEh[c], a2 = pV[c + 1];
-  const float2 b0 = pEv[c], b1 = pC[c], b2 = pEv[c + 1];
-  const float2 c0 = pV[c + R], c1 = pEh[c + R], c2 = pV[c + R + 1];
-  float2 o;
-  o.x = fmaf(ly[0], fmaf(lx[0], a0.x, fmaf(lx[1], a1.x, lx[2] * a2.x)),
-             fmaf(ly[1], fmaf(lx[0], b0.x, fmaf(lx[1], b1.x, lx[2] * b2.x)),
-                  ly[2] * fmaf(lx[0], c0.x, fmaf(lx[1], c1.x, lx[2] * c2.x))));
-  o.y = fmaf(ly[0], fmaf(lx[0], a0.y, fmaf(lx[1], a1.y, lx[2] * a2.y)),
-             fmaf(ly[1], fmaf(lx[0], b0.y, fmaf(lx[1], b1.y, lx[2] * b2.y)),
-                  ly[2] * fmaf(lx[0], c0.y, fmaf(lx[1], c1.y, lx[2] * c2.y))));
-  return o;
+                                           const float2* pC, int c, const float2 lxd[3],
+                                           const float2 lyd[3]) {
+  const float2 v[9] = {pV[c],  pEh[c],     pV[c + 1],  pEv[c],         pC[c],
+                       pEv[c + 1], pV[c + R], pEh[c + R], pV[c + R + 1]};
+  return q2_pair(v, lxd, lyd);
+}
+
+// both lanes of each Lagrange weight
+__device__ __forceinline__ void dup3(const float l[3], float2 d[3]) {
+  d[0] = dup2(l[0]);
+  d[1] = dup2(l[1]);
+  d[2] = dup2(l[2]);
 }
 
 // local coordinates of a point displaced by d (cells) from lattice offset o (0
@@ -466,8 +501,8 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       const int w = AF_IDX(cy * CW + cx, 0, WPL);
 #pragma unroll
       for (int f = 0; f < 3; ++f)
-        W[f * WPL + w] = make_float4(S[(4 * f) * G::SPL], S[(4 * f + 1) * G::SPL],
-                                     S[(4 * f + 2) * G::SPL], S[(4 * f + 3) * G::SPL]);
+        W[f * WPL + w] = rec4(S[(4 * f) * G::SPL], S[(4 * f + 1) * G::SPL],
+                              S[(4 * f + 2) * G::SPL], S[(4 * f + 3) * G::SPL]);
     }
   } else {
     const bool interior = i0 >= 4 && j0 >= 2 && i0 + TX + 4 <= nx && j0 + CH - 2 <= ny &&
@@ -498,7 +533,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
           auto comp = [&](const float4& v) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; };
 #pragma unroll
           for (int f = 0; f < 3; ++f)
-            W[f * WPL + w] = make_float4(comp(pv[f][0]), comp(pv[f][1]), comp(pv[f][2]), comp(pv[f][3]));
+            W[f * WPL + w] = rec4(comp(pv[f][0]), comp(pv[f][1]), comp(pv[f][2]), comp(pv[f][3]));
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             D[q * WPL + w] = comp(av[q]);
@@ -512,8 +547,8 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
         const size_t id = (size_t)wrapi(j0 - 2 + cy, ny) * nx + wrapi(i0 - 2 + cx, nx);
 #pragma unroll
         for (int f = 0; f < 3; ++f)
-          W[f * WPL + t] = make_float4(__ldg(a.in.pt[f][0] + id), __ldg(a.in.pt[f][1] + id),
-                                       __ldg(a.in.pt[f][2] + id), __ldg(a.in.pt[f][3] + id));
+          W[f * WPL + t] = rec4(__ldg(a.in.pt[f][0] + id), __ldg(a.in.pt[f][1] + id),
+                                __ldg(a.in.pt[f][2] + id), __ldg(a.in.pt[f][3] + id));
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           D[q * WPL + t] = __ldg(a.in.avg[q] + id);
@@ -556,7 +591,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
     for (int k = 0; k < 4; ++k) uc[k] = (ub[k] + lo[k]) + (0.0625f * sc[k] + 0.25f * se[k]);
     const Prim<float> w = stored_from_cons_inv(uc, gas, __fdividef(1.f, gas.rho_ref + uc[0]));
     if (!(gas.rho_ref + w.r > 0.f && gas.p_ref + w.p > 0.f)) bad |= FLAG_NONPHYSICAL;
-    W[3 * WPL + c] = make_float4(w.r, w.u, w.v, w.p);
+    W[3 * WPL + c] = rec4(w.r, w.u, w.v, w.p);
     if constexpr (INTER || ADJ) {
       const int gi = i0 - 2 + cx, gj = j0 - 2 + cy;
       if (cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2 && gi < nx && gj < ny) {
@@ -584,7 +619,7 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       const int wc = AF_IDX((dy + 1) * CW + (dx + 1), CW + 1, WPL - CW - 1);
       const int dc = AF_IDX(dy * DCW + dx, 0, DPL);
       const float4 wk = W[fam * WPL + wc];
-      const float rk = gas.rho_ref + wk.x, pk = gas.p_ref + wk.w;
+      const float rk = gas.rho_ref + wk.z, pk = gas.p_ref + wk.w;
       if (!(rk > 0.f && pk > 0.f)) bad |= FLAG_NONPHYSICAL;
       // Z^2 = gamma p rho, c = gamma p / Z: one reciprocal square root (2 ulp)
       const float gp = gas.gamma * pk, z2 = gp * rk;
@@ -594,16 +629,16 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       float Gp[3][4], Guv[3][4];
       if (fam == 0) {
         LoadW<0, CW, WPL> ld = {W, wc};
-        af_sac_V<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
+        af_sac_V<float>(ld, wk.w, wk.x, wk.y, Gp, Guv);
       } else if (fam == 1) {
         LoadW<1, CW, WPL> ld = {W, wc};
-        af_sac_EV<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
+        af_sac_EV<float>(ld, wk.w, wk.x, wk.y, Gp, Guv);
       } else if (fam == 2) {
         LoadW<2, CW, WPL> ld = {W, wc};
-        af_sac_EH<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
+        af_sac_EH<float>(ld, wk.w, wk.x, wk.y, Gp, Guv);
       } else {
         LoadW<3, CW, WPL> ld = {W, wc};
-        af_sac_C<float>(ld, wk.w, wk.y, wk.z, Gp, Guv);
+        af_sac_C<float>(ld, wk.w, wk.x, wk.y, Gp, Guv);
       }
       // stored: the acoustically evolved velocity u + du, v + dv and the
       // pressure increment dp (the velocity increments are only ever added to
@@ -632,12 +667,12 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       const bool own = INTER && dx >= 1 && dx <= TX && dy >= 1 && dy <= TY && gi < nx && gj < ny;
       const size_t gid = own ? (size_t)gj * nx + gi : 0;
       horner(0.5f * r1, d);
-      *D0 = make_float2(wk.y + d[0], wk.z + d[1]);
+      *D0 = make_float2(wk.x + d[0], wk.y + d[1]);
       *D0p = d[2];
       if (own)
         for (int k = 0; k < 3; ++k) a.inc[0][fam][k][gid] = d[k];
       horner(r1, d);
-      *D1 = make_float2(wk.y + d[0], wk.z + d[1]);
+      *D1 = make_float2(wk.x + d[0], wk.y + d[1]);
       *D1p = d[2];
       if (own)
         for (int k = 0; k < 3; ++k) a.inc[1][fam][k][gid] = d[k];
@@ -667,60 +702,63 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       const int wcP = AF_IDX((py + 2) * CW + (px + 2), 0, WPL);  // W cell of the point's cell
       const float4 wp = W[fam * WPL + wcP];
       // first Picard stage from the point's own velocity (Eq. adv-footpoint)
-      const float d1x = -th * wp.y, d1y = -th * wp.z;
-      if (!(fabsf(d1x) <= 1.f && fabsf(d1y) <= 1.f)) bad |= FLAG_REACH;
+      const float2 d1 = __fmul2_rn(dup2(-th), rec_uv(wp));
+      if (!(fabsf(d1.x) <= 1.f && fabsf(d1.y) <= 1.f)) bad |= FLAG_REACH;
       float lx[3], ly[3];
-      int ix = foot_axis(ox, clamp1(d1x), lx), iy = foot_axis(oy, clamp1(d1y), ly);
+      float2 lxd[3], lyd[3];
+      int ix = foot_axis(ox, clamp1(d1.x), lx), iy = foot_axis(oy, clamp1(d1.y), ly);
+      dup3(lx, lxd);
+      dup3(ly, lyd);
       // (a cell's nine nodes reach one row and one column beyond it)
       const int c1 = AF_IDX(wcP + iy * CW + ix, 0, WPL - CW - 1);
       float4 n[9];
       load_cell<CW, WPL>(W, c1, n);
-      const float u1 = AF_Q2(n, y, lx, ly), v1 = AF_Q2(n, z, lx, ly);
+      const float2 uv1 = q2_uv(n, lxd, lyd);
       // the foot
-      const float dfx = -th * u1, dfy = -th * v1;
-      if (!(fabsf(dfx) <= 1.f && fabsf(dfy) <= 1.f)) bad |= FLAG_REACH;
-      ix = foot_axis(ox, clamp1(dfx), lx);
-      iy = foot_axis(oy, clamp1(dfy), ly);
+      const float2 df = __fmul2_rn(dup2(-th), uv1);
+      if (!(fabsf(df.x) <= 1.f && fabsf(df.y) <= 1.f)) bad |= FLAG_REACH;
+      ix = foot_axis(ox, clamp1(df.x), lx);
+      iy = foot_axis(oy, clamp1(df.y), ly);
+      dup3(lx, lxd);
+      dup3(ly, lyd);
       const int c2 = AF_IDX(wcP + iy * CW + ix, 0, WPL - CW - 1);
       if (c2 != c1) load_cell<CW, WPL>(W, c2, n);
-      const float rft = AF_Q2(n, x, lx, ly), pft = AF_Q2(n, w, lx, ly);  // rho~_f, p~_f
+      const float2 rpf = q2_rp(n, lxd, lyd);  // rho~_f, p~_f
+      const float rft = rpf.x, pft = rpf.y;
       Prim<float> nw;
       if (a.variant == 0) {
         // transported increment at the foot; rho from dp / c_f^2 (Sec. 6.1 step 4):
         // u_f + du_f = I_h(u + du)(P_f) since both interpolants share the basis
         const int dcf = AF_IDX((py + 1 + iy) * DCW + (px + 1 + ix), 0, DPL - DCW - 1);
-        float e[3];
-        {
-          const float2 e01 = q2_eval2<DCW>(reinterpret_cast<const float2*>(Ds),
-                                           reinterpret_cast<const float2*>(Ds + 3 * DPL),
-                                           reinterpret_cast<const float2*>(Ds + 6 * DPL),
-                                           reinterpret_cast<const float2*>(Ds + 9 * DPL), dcf, lx,
-                                           ly);
-          e[0] = e01.x;
-          e[1] = e01.y;
-        }
-        e[2] = q2_eval<DCW>(Ds + 2 * DPL, Ds + 5 * DPL, Ds + 8 * DPL, Ds + 11 * DPL, dcf, lx, ly);
+        const float2 e01 = q2_eval2<DCW>(reinterpret_cast<const float2*>(Ds),
+                                         reinterpret_cast<const float2*>(Ds + 3 * DPL),
+                                         reinterpret_cast<const float2*>(Ds + 6 * DPL),
+                                         reinterpret_cast<const float2*>(Ds + 9 * DPL), dcf, lxd,
+                                         lyd);
+        const float e2 =
+            q2_eval<DCW>(Ds + 2 * DPL, Ds + 5 * DPL, Ds + 8 * DPL, Ds + 11 * DPL, dcf, lx, ly);
         const float rf = gas.rho_ref + rft, pf = gas.p_ref + pft;
         if (!(rf > 0.f && pf > 0.f)) bad |= FLAG_NONPHYSICAL;
-        nw.r = rft + __fdividef(e[2] * rf, gas.gamma * pf);
-        nw.u = e[0];
-        nw.v = e[1];
-        nw.p = pft + e[2];
+        nw.r = rft + __fdividef(e2 * rf, gas.gamma * pf);
+        nw.u = e01.x;
+        nw.v = e01.y;
+        nw.p = pft + e2;
       } else {
         // additive update (Eq. barsukow-additive), acoustic rho closure at P
         const int dcp = AF_IDX((py + 1) * DCW + (px + 1), 0, DPL);
         const float2 uv = reinterpret_cast<const float2*>(Ds + fam * 3 * DPL)[dcp];
-        const float du = uv.x - wp.y;
-        const float dv = uv.y - wp.z;
+        const float du = uv.x - wp.x;
+        const float dv = uv.y - wp.y;
         const float dp = Ds[(fam * 3 + 2) * DPL + dcp];
-        nw.r = rft + __fdividef(dp * (gas.rho_ref + wp.x), gas.gamma * (gas.p_ref + wp.w));
-        nw.u = AF_Q2(n, y, lx, ly) + du;
-        nw.v = AF_Q2(n, z, lx, ly) + dv;
+        nw.r = rft + __fdividef(dp * (gas.rho_ref + wp.z), gas.gamma * (gas.p_ref + wp.w));
+        const float2 uvf = q2_uv(n, lxd, lyd);
+        nw.u = uvf.x + du;
+        nw.v = uvf.y + dv;
         nw.p = pft + dp;
       }
       if (!(isfinite(nw.r) && isfinite(nw.u) && isfinite(nw.v) && isfinite(nw.p)))
         bad |= FLAG_NONFINITE;
-      res[k] = make_float4(nw.r, nw.u, nw.v, nw.p);
+      res[k] = rec4(nw.r, nw.u, nw.v, nw.p);
       // owned points at t^{n+1} go straight to HBM
       const int gi = i0 + px, gj = j0 + py;
       if ((INTER || ADJ) && s == 0 && px < TX && py < TY && gi < nx && gj < ny) {
