@@ -213,8 +213,7 @@ const char *af_status_string(af_status s);
  * static device array of about 6.3 MB that every GPU loading the library holds
  * until the process exits); no cudaMalloc, cudaFree or other allocating call
  * is made.  The first call on a device looks up the work area's address on
- * that device; make that first call before any stream capture.  Every call
- * shares the one work area: calls that overlap on the GPU (other streams,
+ * that device.  Every call shares the one work area: calls that overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  Every call clears
  * the work area's error word, enqueues the step on `cuda_stream`, then copies
  * the error word to the host and synchronises `cuda_stream` before it returns
