@@ -11,8 +11,10 @@ e2e        the same metric through the public API with host buffers: every step
            copies its state in from pinned host memory, advances it and copies
            the result back out (af_exchange_state overlaps one step's outgoing
            copy with the next step's incoming one); the median of three timed
-           runs (max over ranks).  link_ms_per_step: the same transfers alone
-           (both directions at once, no compute), the bound of this leg.
+           runs (max over ranks).  async_exchange_ms_per_step: the same with
+           af_exchange_state_async, which enqueues the exchange and returns at
+           once.  link_ms_per_step: the same transfers alone (both directions
+           at once, no compute), the bound of this leg.
 roofline   the dominant kernel (the fused step kernel), timed per launch with CUDA
            events: its algorithmic FP32 lane operations per launch / duration
            against 152 SMs x 128 FP32 lanes x SM clock ("alu", the bound), and
@@ -425,35 +427,46 @@ def main():
     host_out = torch.empty_like(host_in).pin_memory()
     e2e_steps = max(1, args.e2e_steps)
 
-    def e2e_run(n):
+    def e2e_run(n, exchange):
         # every step's input goes in and its result comes out; one call hands a
         # step's result out while the next step's input comes in, the two
-        # transfers overlapping on the link (and the result's with the next step)
+        # transfers overlapping on the link (and the result's with the next step);
+        # the final get waits for every transfer of the run
         solver.set_state(host_in)
         for i in range(n):
             solver.step(P.dt, 1)
             if i + 1 < n:
-                solver.exchange(host_out, host_in)
+                exchange(host_out, host_in)
             else:
                 solver.state(host_out)
         torch.cuda.synchronize()
 
-    e2e_run(2)  # first use allocates the exchange's staging buffer and streams
-    # three timed runs, the median (the host side of the link is shared with
-    # other work on the node and varies from run to run)
-    runs = []
-    for _ in range(3):
-        barrier()
-        t0 = time.perf_counter()
-        e2e_run(e2e_steps)
-        runs.append(time.perf_counter() - t0)
+    def e2e_runs(exchange):
+        e2e_run(2, exchange)  # first use allocates the staging buffers and streams
+        # three timed runs, the median (the host side of the link is shared with
+        # other work on the node and varies from run to run)
+        runs = []
+        for _ in range(3):
+            barrier()
+            t0 = time.perf_counter()
+            e2e_run(e2e_steps, exchange)
+            runs.append(time.perf_counter() - t0)
+        return runs
+
+    # af_exchange_state (returns with the new state in place) and, beside it,
+    # its enqueued form af_exchange_state_async
+    runs = e2e_runs(solver.exchange)
+    runs_async = e2e_runs(solver.exchange_async)
     e2e_ms, e2e_value = aggregate(1e3 * sorted(runs)[1], N, e2e_steps, world, "cuda")
+    async_ms, _ = aggregate(1e3 * sorted(runs_async)[1], N, e2e_steps, world, "cuda")
     link_ms = link_copy_ms(torch, host_in, host_out)
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(host_in.numel() * 8),
            "d2h_bytes_per_step": int(host_out.numel() * 8),
            "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps,
            "runs_ms_per_step": [round(1e3 * r / e2e_steps, 3) for r in runs],
+           "api": "af_exchange_state per step (host planes, pinned)",
+           "async_exchange_ms_per_step": async_ms / e2e_steps,
            "link_ms_per_step": link_ms,
            "link_frac": link_ms / (e2e_ms / e2e_steps),
            "link_note": "link_ms_per_step: one step's input planes copied in and its result "

@@ -163,7 +163,8 @@ af_status af_set_state(af_handle *h, const af_state_f64 *in, af_memory where);
  * AF_DEVICE: `out` is complete on return too.
  * AF_HOST: both transfers run on copy engines on two streams of the handle, so
  * that they overlap on the host-device link with each other and with a step
- * still running: `in` is copied into a device staging buffer at once, the
+ * still running (one copy per direction when the sixteen planes are
+ * consecutive in memory, in plane order, else one per plane): `in` is copied into a device staging buffer at once, the
  * outgoing state is converted into a second one (16 FP64 planes each,
  * allocated on first use, held until af_destroy) and copied into `out`.  That
  * last copy may still be in flight on return; later calls of this handle that
@@ -173,6 +174,24 @@ af_status af_set_state(af_handle *h, const af_state_f64 *in, af_memory where);
  * af_exchange_state, has returned.  `in` is read before the call returns. */
 af_status af_exchange_state(af_handle *h, const af_state_f64 *out, const af_state_f64 *in,
                             af_memory where);
+
+/* Asynchronous form of af_exchange_state for host planes (pinned or pageable),
+ * for callers that stream states through the solver: `out` <- the current
+ * state, then the current state <- `in`, all enqueued without waiting, so that
+ * consecutive calls keep both directions of the host-device link busy.  The
+ * incoming planes are copied into one of two device staging buffers and the
+ * outgoing state is converted into one of two others (16 FP64 planes each,
+ * allocated on the first call, held until af_destroy); alternate calls use
+ * alternate buffers, each reused once its earlier copy and conversion are done.
+ * The handle's later steps run on the new state.  The call returns before the
+ * transfers end: the caller may modify `in` or read `out` only after af_sync
+ * (or any other call of this handle except af_step and the exchanges) has
+ * returned.  An incoming plane that shares memory with the target of an
+ * earlier exchange's outgoing copy is read after that copy.  Unlike
+ * af_exchange_state it leaves the latched device error as it is (af_sync
+ * reports it; af_set_state clears it).  `out` and `in` may not share a byte
+ * (AF_ERR_ARG). */
+af_status af_exchange_state_async(af_handle *h, const af_state_f64 *out, const af_state_f64 *in);
 
 /* FP64 global diagnostics of the current state, out[AF_NINV] in host memory.
  * Synchronises the stream. */

@@ -73,6 +73,9 @@ def load():
         lib.af_exchange_state.argtypes = [vp, ctypes.POINTER(AfState), ctypes.POINTER(AfState),
                                           ctypes.c_int]
         lib.af_exchange_state.restype = ctypes.c_int
+        lib.af_exchange_state_async.argtypes = [vp, ctypes.POINTER(AfState),
+                                                ctypes.POINTER(AfState)]
+        lib.af_exchange_state_async.restype = ctypes.c_int
         lib.af_reduce_invariants.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.af_reduce_invariants.restype = ctypes.c_int
         lib.af_adjoint_step.argtypes = [vp, d, ctypes.POINTER(AfState), ctypes.POINTER(AfState),
@@ -184,6 +187,18 @@ def af_exchange_state(handle, out, state):
                                      AF_DEVICE if din else AF_HOST)
 
 
+def af_exchange_state_async(handle, out, state):
+    """Enqueued form of af_exchange_state for host arrays (16, ny, nx) float64:
+    `out` may be read and `state` modified only after af_sync."""
+    pout, dout = _array_ptr(out)
+    pin, din = _array_ptr(state)
+    assert not dout and not din, "af_exchange_state_async takes host arrays"
+    n = state.shape[1] * state.shape[2]
+    so, si = _state_struct(pout, n), _state_struct(pin, n)
+    return load().af_exchange_state_async(ctypes.c_void_p(handle), ctypes.byref(so),
+                                           ctypes.byref(si))
+
+
 def af_reduce_invariants(handle, out):
     """out: float64 numpy array of AF_NINV values (host)."""
     import numpy as np
@@ -253,6 +268,15 @@ class Solver:
         rc = af_exchange_state(self.handle, out, state)
         if rc != AF_OK:
             raise AfError(rc, "af_exchange_state")
+        return out
+
+    def exchange_async(self, out, state):
+        """Enqueue handing the current state out into `out` and taking `state`
+        in (see af_exchange_state_async): `out` holds the result and `state` may
+        be reused once sync() has returned."""
+        rc = af_exchange_state_async(self.handle, out, state)
+        if rc != AF_OK:
+            raise AfError(rc, "af_exchange_state_async")
         return out
 
     def invariants(self):

@@ -67,6 +67,17 @@ struct af_handle {
                          // pipelined step reports its first staged-tile wait as timed out
   int out_pending;       // 1: the outgoing copies of the last exchange may be in flight
   af_state_f64 pending_out;  // ... into these planes
+  // af_exchange_state_async (lazy): two incoming and two outgoing staging
+  // buffers of 16 FP64 planes, used by alternate calls
+  double* astage[2];
+  double* axstage[2];
+  cudaEvent_t ev_staged[2];    // the incoming copy into astage[b] is done
+  cudaEvent_t ev_imported[2];  // the import that read astage[b] is done (astage[b] free)
+  cudaEvent_t ev_exported[2];  // the export into axstage[b] is done
+  cudaEvent_t ev_sent[2];      // the outgoing copy from axstage[b] is done (axstage[b] free)
+  int abuf;                    // buffer of the next asynchronous exchange
+  int apending[2];             // 1: the outgoing copy of buffer b may be in flight ...
+  af_state_f64 apending_out[2];  // ... into these planes
 };
 
 namespace {
@@ -261,6 +272,41 @@ af_status check_state_ptrs(const af_state_f64* s) {
 
 const double* plane_in(const af_state_f64* s, int p) { return state_plane(s, p); }
 
+// true when plane p of `s` starts p * N doubles after plane 0 for every p (the
+// sixteen planes of one (16, ny, nx) array)
+bool planes_consecutive(const af_state_f64* s, size_t N) {
+  for (int p = 1; p < 16; ++p)
+    if (plane_in(s, p) != plane_in(s, 0) + (size_t)p * N) return false;
+  return true;
+}
+
+// Copies the sixteen planes (N doubles each) of `src` into those of `dst` on
+// stream `st`: one copy when both are consecutive, else one copy per plane.
+cudaError_t copy_planes(const af_state_f64* dst, const af_state_f64* src, size_t N,
+                        cudaMemcpyKind kind, cudaStream_t st) {
+  if (planes_consecutive(dst, N) && planes_consecutive(src, N))
+    return cudaMemcpyAsync((void*)plane_in(dst, 0), plane_in(src, 0), sizeof(double) * 16 * N,
+                           kind, st);
+  for (int p = 0; p < 16; ++p) {
+    const cudaError_t e =
+        cudaMemcpyAsync((void*)plane_in(dst, p), plane_in(src, p), sizeof(double) * N, kind, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// the sixteen consecutive planes starting at `base`, as a state descriptor
+af_state_f64 planes_at(double* base, size_t N) {
+  af_state_f64 s;
+  for (int k = 0; k < 4; ++k) {
+    s.avg[k] = base + (size_t)k * N;
+    s.vtx[k] = base + (size_t)(4 + k) * N;
+    s.ev[k] = base + (size_t)(8 + k) * N;
+    s.eh[k] = base + (size_t)(12 + k) * N;
+  }
+  return s;
+}
+
 af_status ensure_staging(af_handle* h) {
   if (h->staging) return AF_OK;
   if (cudaMalloc(&h->staging, sizeof(double) * 16 * h->N) != cudaSuccess) {
@@ -321,10 +367,22 @@ af_status import_enqueue(af_handle* h, const af_state_f64* in, af_memory where) 
   return AF_OK;
 }
 
-// Orders the handle's stream after the outgoing copies of the last
-// af_exchange_state, which may still be in flight on the aux stream.
+// True if `in` shares a byte with the target of an outgoing copy of an
+// exchange that may still be in flight.
+bool overlaps_pending_out(const af_handle* h, const af_state_f64* in) {
+  const size_t bytes = sizeof(double) * h->N;
+  if (h->out_pending && state_planes_overlap(&h->pending_out, in, bytes)) return true;
+  for (int b = 0; b < 2; ++b)
+    if (h->apending[b] && state_planes_overlap(&h->apending_out[b], in, bytes)) return true;
+  return false;
+}
+
+// Orders the handle's stream after the outgoing copies of earlier exchanges
+// (af_exchange_state, af_exchange_state_async), which may still be in flight
+// on the aux stream (ev_join follows the latest of them).
 af_status wait_outgoing(af_handle* h) {
-  if (h->out_pending && cudaStreamWaitEvent(h->stream, h->ev_join, 0) != cudaSuccess)
+  if ((h->out_pending || h->apending[0] || h->apending[1]) &&
+      cudaStreamWaitEvent(h->stream, h->ev_join, 0) != cudaSuccess)
     return cuda_fail(h);
   return AF_OK;
 }
@@ -337,6 +395,7 @@ af_status import_finish(af_handle* h) {
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h);
   *(volatile unsigned*)h->h_flags = 0;
   h->out_pending = 0;
+  h->apending[0] = h->apending[1] = 0;
   return AF_OK;
 }
 
@@ -664,6 +723,7 @@ af_status af_sync(af_handle* h) {
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return cuda_fail(h);
   h->out_pending = 0;
+  h->apending[0] = h->apending[1] = 0;
   return map_flags(*(volatile unsigned*)h->h_flags);
 }
 
@@ -708,6 +768,24 @@ af_status af_get_state(af_handle* h, const af_state_f64* out, af_memory where) {
   return af_sync(h);
 }
 
+}  // extern "C"
+namespace {
+
+// The copy streams and events of the exchanges (created on first use).
+af_status ensure_aux(af_handle* h) {
+  if (h->aux) return AF_OK;
+  if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->aux_in, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess)
+    return AF_ERR_CUDA;
+  return AF_OK;
+}
+
+}  // namespace
+extern "C" {
+
 af_status af_exchange_state(af_handle* h, const af_state_f64* out, const af_state_f64* in,
                             af_memory where) {
   NvtxRange range("af_exchange_state");
@@ -737,31 +815,15 @@ af_status af_exchange_state(af_handle* h, const af_state_f64* out, const af_stat
   }
   af_status st = ensure_staging(h);
   if (st != AF_OK) return st;
-  if (!h->aux) {
-    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&h->aux_in, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess)
-      return cuda_fail(h);
-  }
-  // an incoming plane that is also the target of the last exchange's outgoing
-  // copies is read after them
-  if (h->out_pending && state_planes_overlap(&h->pending_out, in, sizeof(double) * h->N) &&
-      cudaStreamWaitEvent(h->aux_in, h->ev_join, 0) != cudaSuccess)
+  if (ensure_aux(h) != AF_OK) return cuda_fail(h);
+  // an incoming plane that is also the target of an earlier exchange's
+  // outgoing copies is read after them
+  if (overlaps_pending_out(h, in) && cudaStreamWaitEvent(h->aux_in, h->ev_join, 0) != cudaSuccess)
     return cuda_fail(h);
   // the staging buffer is idle: every earlier call that used it has synchronised
-  af_state_f64 staged;
-  for (int k = 0; k < 4; ++k) {
-    staged.avg[k] = h->staging + (size_t)k * h->N;
-    staged.vtx[k] = h->staging + (size_t)(4 + k) * h->N;
-    staged.ev[k] = h->staging + (size_t)(8 + k) * h->N;
-    staged.eh[k] = h->staging + (size_t)(12 + k) * h->N;
-  }
-  for (int p = 0; p < 16; ++p)
-    if (cudaMemcpyAsync((void*)plane_in(&staged, p), plane_in(in, p), sizeof(double) * h->N,
-                        cudaMemcpyHostToDevice, h->aux_in) != cudaSuccess)
-      return cuda_fail(h);
+  const af_state_f64 staged = planes_at(h->staging, h->N);
+  if (copy_planes(&staged, in, h->N, cudaMemcpyHostToDevice, h->aux_in) != cudaSuccess)
+    return cuda_fail(h);
   if (cudaEventRecord(h->ev_in, h->aux_in) != cudaSuccess) return cuda_fail(h);
   F64Out dst;
   for (int p = 0; p < 16; ++p) dst.p[p] = h->xstaging + (size_t)p * h->N;
@@ -770,10 +832,9 @@ af_status af_exchange_state(af_handle* h, const af_state_f64* out, const af_stat
   if (cudaEventRecord(h->ev_fork, h->stream) != cudaSuccess ||
       cudaStreamWaitEvent(h->aux, h->ev_fork, 0) != cudaSuccess)
     return cuda_fail(h);
-  for (int p = 0; p < 16; ++p)
-    if (cudaMemcpyAsync((void*)plane_in(out, p), dst.p[p], sizeof(double) * h->N,
-                        cudaMemcpyDeviceToHost, h->aux) != cudaSuccess)
-      return cuda_fail(h);
+  const af_state_f64 xs = planes_at(h->xstaging, h->N);
+  if (copy_planes(out, &xs, h->N, cudaMemcpyDeviceToHost, h->aux) != cudaSuccess)
+    return cuda_fail(h);
   if (cudaEventRecord(h->ev_join, h->aux) != cudaSuccess ||
       cudaStreamWaitEvent(h->stream, h->ev_in, 0) != cudaSuccess)
     return cuda_fail(h);
@@ -784,6 +845,72 @@ af_status af_exchange_state(af_handle* h, const af_state_f64* out, const af_stat
     h->pending_out = *out;
   }
   return st;
+}
+
+af_status af_exchange_state_async(af_handle* h, const af_state_f64* out,
+                                  const af_state_f64* in) {
+  NvtxRange range("af_exchange_state_async");
+  if (!h || check_state_ptrs(out) != AF_OK || check_state_ptrs(in) != AF_OK) return AF_ERR_ARG;
+  if (state_planes_overlap(out, in, sizeof(double) * h->N)) return AF_ERR_ARG;
+  if (h->broken) return AF_ERR_STATE;
+  DeviceGuard guard(h->device);
+  if (ensure_aux(h) != AF_OK) return cuda_fail(h);
+  if (!h->astage[0]) {
+    const size_t bytes = sizeof(double) * 16 * h->N;
+    for (int b = 0; b < 2; ++b) {
+      if (cudaMalloc(&h->astage[b], bytes) != cudaSuccess) h->astage[b] = nullptr;
+      if (cudaMalloc(&h->axstage[b], bytes) != cudaSuccess) h->axstage[b] = nullptr;
+    }
+    if (!h->astage[0] || !h->astage[1] || !h->axstage[0] || !h->axstage[1]) {
+      for (int b = 0; b < 2; ++b) {
+        if (h->astage[b]) cudaFree(h->astage[b]);
+        if (h->axstage[b]) cudaFree(h->axstage[b]);
+        h->astage[b] = h->axstage[b] = nullptr;
+      }
+      return AF_ERR_ALLOC;
+    }
+    for (int b = 0; b < 2; ++b)
+      if (cudaEventCreateWithFlags(&h->ev_staged[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_imported[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_exported[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_sent[b], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(h);
+  }
+  const int b = h->abuf;
+  const size_t N = h->N;
+  const af_state_f64 staged = planes_at(h->astage[b], N);
+  // incoming: into astage[b] once the import that last read it is done, and
+  // after any outgoing copy still writing the planes it reads
+  if (overlaps_pending_out(h, in) && cudaStreamWaitEvent(h->aux_in, h->ev_join, 0) != cudaSuccess)
+    return cuda_fail(h);
+  if (cudaStreamWaitEvent(h->aux_in, h->ev_imported[b], 0) != cudaSuccess) return cuda_fail(h);
+  if (copy_planes(&staged, in, N, cudaMemcpyHostToDevice, h->aux_in) != cudaSuccess)
+    return cuda_fail(h);
+  if (cudaEventRecord(h->ev_staged[b], h->aux_in) != cudaSuccess) return cuda_fail(h);
+  // outgoing: the current state into axstage[b] once its last copy out is done
+  F64Out dst;
+  for (int p = 0; p < 16; ++p) dst.p[p] = h->axstage[b] + (size_t)p * N;
+  if (cudaStreamWaitEvent(h->stream, h->ev_sent[b], 0) != cudaSuccess) return cuda_fail(h);
+  af_status st = export_enqueue(h, dst);
+  if (st != AF_OK) return st;
+  if (cudaEventRecord(h->ev_exported[b], h->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(h->aux, h->ev_exported[b], 0) != cudaSuccess)
+    return cuda_fail(h);
+  const af_state_f64 xs = planes_at(h->axstage[b], N);
+  if (copy_planes(out, &xs, N, cudaMemcpyDeviceToHost, h->aux) != cudaSuccess)
+    return cuda_fail(h);
+  if (cudaEventRecord(h->ev_sent[b], h->aux) != cudaSuccess ||
+      cudaEventRecord(h->ev_join, h->aux) != cudaSuccess)
+    return cuda_fail(h);
+  // the new state, on the handle's stream after the incoming copy
+  if (cudaStreamWaitEvent(h->stream, h->ev_staged[b], 0) != cudaSuccess) return cuda_fail(h);
+  st = import_enqueue(h, &staged, AF_DEVICE);
+  if (st != AF_OK) return st;
+  if (cudaEventRecord(h->ev_imported[b], h->stream) != cudaSuccess) return cuda_fail(h);
+  h->apending[b] = 1;
+  h->apending_out[b] = *out;
+  h->abuf = 1 - b;
+  return cudaGetLastError() == cudaSuccess ? AF_OK : cuda_fail(h);
 }
 
 af_status af_reduce_invariants(af_handle* h, double* out) {
@@ -864,6 +991,16 @@ void af_destroy(af_handle* h) {
   if (h->d_red) cudaFree(h->d_red);
   if (h->adj_arena) cudaFree(h->adj_arena);
   if (h->xstaging) cudaFree(h->xstaging);
+  if (h->astage[0]) {
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(h->astage[b]);
+      cudaFree(h->axstage[b]);
+      cudaEventDestroy(h->ev_staged[b]);
+      cudaEventDestroy(h->ev_imported[b]);
+      cudaEventDestroy(h->ev_exported[b]);
+      cudaEventDestroy(h->ev_sent[b]);
+    }
+  }
   if (h->aux) {
     cudaStreamDestroy(h->aux);
     cudaStreamDestroy(h->aux_in);

@@ -519,6 +519,70 @@ def test_exchange_is_get_then_set(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_comp"])
+def test_exchange_async_streams_like_the_synchronous_exchange(precision):
+    """af_exchange_state_async: a stream of distinct inputs, each stepped once
+    and handed out by the next call (both staging buffers of each direction in
+    turn), gives bitwise the one-step results of the inputs, for pinned and
+    pageable host planes; a chain where one call's output is the next call's
+    input, and an output buffer reused while its copy may be in flight, gives
+    the synchronous exchange's results; overlapping planes are refused."""
+    import torch
+    X = [I.random_smooth(68, 40, seed=50 + k, amp=0.05) for k in range(5)]
+    dt = 0.9 * min(P.dt for P in X)  # one time step for every input
+    ref = af.Solver(X[0].grid, X[0].gamma, X[0].state, precision=precision)
+    want = []
+    for P in X:
+        ref.set_state(P.state)
+        ref.step(dt, 1)
+        want.append(ref.state())
+    ref.close()
+    for kind in ("pinned", "pageable"):
+        if kind == "pinned":
+            ins = [torch.from_numpy(P.state.copy()).pin_memory() for P in X]
+            outs = [torch.empty_like(ins[0]).pin_memory() for _ in X]
+        else:
+            ins = [P.state.copy() for P in X]
+            outs = [np.empty_like(X[0].state) for _ in X]
+        s = af.Solver(X[0].grid, X[0].gamma, X[0].state, precision=precision)
+        s.set_state(ins[0])
+        for k in range(4):
+            s.step(dt, 1)
+            s.exchange_async(outs[k], ins[k + 1])
+        s.step(dt, 1)
+        s.sync()
+        for k in range(4):
+            got = outs[k].numpy() if hasattr(outs[k], "numpy") else outs[k]
+            assert np.array_equal(got, want[k]), (kind, k)
+        assert np.array_equal(s.state(), want[4]), kind
+        with pytest.raises(af.AfError):
+            s.exchange_async(ins[0], ins[0])
+        s.close()
+    # chained buffers, as in the synchronous chain below: the same calls through
+    # both exchanges give the same bits (a state taken back in has made the
+    # round trip through its FP64 planes on both paths)
+    P, Q = X[0], X[1]
+
+    def chain(exchange_name):
+        A = torch.empty(P.state.shape, dtype=torch.float64).pin_memory()
+        B = torch.from_numpy(Q.state.copy()).pin_memory()
+        C = torch.empty_like(A).pin_memory()
+        s = af.Solver(P.grid, P.gamma, P.state, precision=precision)
+        exchange = getattr(s, exchange_name)
+        s.step(dt, 1)
+        exchange(A, B)  # A <- S1 (in flight), state <- Q
+        exchange(C, A)  # C <- Q, state <- A = S1 once it has arrived
+        s.step(dt, 1)
+        exchange(C, B)  # C <- S2 while the previous copy into C may be in flight
+        s.sync()
+        out = (A.numpy().copy(), C.numpy().copy(), s.state())
+        s.close()
+        return out
+
+    for got, want_ in zip(chain("exchange_async"), chain("exchange")):
+        assert np.array_equal(got, want_)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_comp"])
 def test_exchange_chain_through_pinned_buffers(precision):
     """Streaming through host buffers: the state handed out by one exchange is
     taken back in by the next (whose incoming copy must wait for that outgoing
