@@ -455,14 +455,12 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
   af_status st = ensure_staging(h);
   if (st != AF_OK) return st;
   Cast16<double, T> cin;
+  const af_state_f64 staged = planes_at(h->staging, h->N);
+  if (where == AF_HOST &&
+      copy_planes(&staged, lin, h->N, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cuda_fail(h);
   for (int p = 0; p < 16; ++p) {
-    const double* src = plane_in(lin, p);
-    if (where == AF_HOST) {
-      if (cudaMemcpyAsync(h->staging + (size_t)p * h->N, src, sizeof(double) * h->N,
-                          cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return cuda_fail(h);
-      src = h->staging + (size_t)p * h->N;
-    }
+    const double* src = where == AF_HOST ? plane_in(&staged, p) : plane_in(lin, p);
     cin.src[p] = src;
     cin.dst[p] = v.lam + (size_t)(LAM_IN + p) * v.ps;
     v.lin64[p] = src;
@@ -493,11 +491,9 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
       for (int p = 0; p < 16; ++p)
         out.dst[p] = where == AF_HOST ? h->staging + (size_t)p * h->N : (double*)plane_in(lout, p);
       k_adj_out<T><<<grid1d(h->N), 256, 0, s>>>(v, out, h->N);
-      if (where == AF_HOST)
-        for (int p = 0; p < 16; ++p)
-          if (cudaMemcpyAsync((void*)plane_in(lout, p), h->staging + (size_t)p * h->N,
-                              sizeof(double) * h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-            return cuda_fail(h);
+      if (where == AF_HOST &&
+          copy_planes(lout, &staged, h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return cuda_fail(h);
       if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
       return adjoint_done(h);
     }
@@ -547,11 +543,9 @@ af_status adjoint_impl(af_handle* h, double dt, const af_state_f64* lin, const a
   for (int p = 0; p < 16; ++p)
     out.dst[p] = where == AF_HOST ? h->staging + (size_t)p * h->N : (double*)plane_in(lout, p);
   k_adj_out<T><<<grid1d(h->N), 256, 0, s>>>(v, out, h->N);
-  if (where == AF_HOST)
-    for (int p = 0; p < 16; ++p)
-      if (cudaMemcpyAsync((void*)plane_in(lout, p), h->staging + (size_t)p * h->N,
-                          sizeof(double) * h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return cuda_fail(h);
+  if (where == AF_HOST &&
+      copy_planes(lout, &staged, h->N, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cuda_fail(h);
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
   return adjoint_done(h);
 }
