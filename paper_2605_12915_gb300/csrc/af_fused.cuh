@@ -684,7 +684,9 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
   // duration by duration; the points of duration s replace D(s) once every
   // thread is done reading it.  The nine nodes of the first Picard stage's
   // cell are loaded once and reused for the foot when it lies in the same cell.
-  constexpr int NPTS = G::NPTS;
+  // (ADJ: the owned points only, the ones the reverse sweep reads; the others
+  // serve the edge fluxes, which ADJ does not form)
+  constexpr int NPTS = ADJ ? 3 * TX * TY : G::NPTS;
   constexpr int PER = (NPTS + NT - 1) / NT;
   const float th_full = a.dt / a.h;
 #pragma unroll 1
@@ -697,7 +699,14 @@ __device__ __forceinline__ bool fused_tile(const StepArgs<float>& a, PipeCtx& pc
       const int t = threadIdx.x + k * NT;
       if (k >= NPTS / NT && t >= NPTS) break;  // rounds k < NPTS / NT are full (NT threads)
       int fam, px, py;
-      point_item<PW, G::PH>(t, fam, px, py);
+      if constexpr (ADJ) {
+        fam = t / (TX * TY);
+        const int u = t - fam * (TX * TY);
+        px = u % TX;
+        py = u / TX;
+      } else {
+        point_item<PW, G::PH>(t, fam, px, py);
+      }
       const int ox = fam == 2 ? 1 : 0, oy = fam == 1 ? 1 : 0;
       const int wcP = AF_IDX((py + 2) * CW + (px + 2), 0, WPL);  // W cell of the point's cell
       const float4 wp = W[fam * WPL + wcP];
