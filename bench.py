@@ -10,11 +10,14 @@ value      device-timed cell-updates/s of K steps (CUDA events on the solver's
 e2e        the same metric through the public API with host buffers: every step
            copies its state in from pinned host memory, advances it and copies
            the result back out (af_exchange_state overlaps one step's outgoing
-           copy with the next step's incoming one); the median of three timed
-           runs (max over ranks).  async_exchange_ms_per_step: the same with
-           af_exchange_state_async, which enqueues the exchange and returns at
-           once.  link_ms_per_step: the same transfers alone (both directions
-           at once, no compute), the bound of this leg.
+           copy with the next step's incoming one; af_exchange_state_async
+           enqueues it all, so that consecutive steps' transfers queue back to
+           back); the run ends with a get of the last result, which waits for
+           every transfer; the median of three timed runs (max over ranks).
+           sync_exchange_ms_per_step: the same with af_exchange_state, which
+           returns with the new state in place.  link_ms_per_step: the same
+           transfers alone (both directions at once, no compute), the bound of
+           this leg.
 roofline   the dominant kernel (the fused step kernel), timed per launch with CUDA
            events: its algorithmic FP32 lane operations per launch / duration
            against 152 SMs x 128 FP32 lanes x SM clock ("alu", the bound), and
@@ -453,20 +456,22 @@ def main():
             runs.append(time.perf_counter() - t0)
         return runs
 
-    # af_exchange_state (returns with the new state in place) and, beside it,
-    # its enqueued form af_exchange_state_async
-    runs = e2e_runs(solver.exchange)
-    runs_async = e2e_runs(solver.exchange_async)
+    # af_exchange_state_async (the exchange enqueued, so that consecutive steps'
+    # transfers queue back to back) and, beside it, af_exchange_state (returns
+    # with the new state in place)
+    runs = e2e_runs(solver.exchange_async)
+    runs_sync = e2e_runs(solver.exchange)
     e2e_ms, e2e_value = aggregate(1e3 * sorted(runs)[1], N, e2e_steps, world, "cuda")
-    async_ms, _ = aggregate(1e3 * sorted(runs_async)[1], N, e2e_steps, world, "cuda")
+    sync_ms, _ = aggregate(1e3 * sorted(runs_sync)[1], N, e2e_steps, world, "cuda")
     link_ms = link_copy_ms(torch, host_in, host_out)
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(host_in.numel() * 8),
            "d2h_bytes_per_step": int(host_out.numel() * 8),
            "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps,
            "runs_ms_per_step": [round(1e3 * r / e2e_steps, 3) for r in runs],
-           "api": "af_exchange_state per step (host planes, pinned)",
-           "async_exchange_ms_per_step": async_ms / e2e_steps,
+           "api": "af_exchange_state_async per step (host planes, pinned); the run "
+                  "ends with af_get_state, which waits for every transfer",
+           "sync_exchange_ms_per_step": sync_ms / e2e_steps,
            "link_ms_per_step": link_ms,
            "link_frac": link_ms / (e2e_ms / e2e_steps),
            "link_note": "link_ms_per_step: one step's input planes copied in and its result "
@@ -515,7 +520,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof,
             "e2e": e2e,
-            "gpu_launches": kstats["launches_per_step"] * args.steps,
+            # the steps' kernels, and the one that copies the error word to the
+            # host at the end of the af_step call
+            "gpu_launches": kstats["launches_per_step"] * args.steps + 1,
             "clocks": csum,
             "fp64": fp64,
             "adjoint": adjoint,

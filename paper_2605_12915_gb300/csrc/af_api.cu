@@ -46,6 +46,7 @@ struct af_handle {
   double* staging;       // 16 FP64 planes for host/device exchange (lazy)
   unsigned* d_flags;
   unsigned* h_flags;     // pinned mirror, written asynchronously after each step
+  unsigned* h_flags_dev; // the device's address of that mirror
   double* d_red;         // reduction partials + result
   double* h_red;         // pinned
   int red_blocks;
@@ -89,6 +90,18 @@ struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
   ~NvtxRange() { nvtxRangePop(); }
 };
+
+// Copies the device error word into the host's pinned mirror by a store
+// through the device's mapping of page-locked memory.  No copy engine takes
+// part, so the copy never waits behind large host-bound copies in flight on
+// the exchange streams (a cudaMemcpyAsync of the word can queue behind them
+// and hold up the step stream for a whole state transfer).
+__global__ void k_flags_to_host(const unsigned* d, unsigned* h) {
+  if (threadIdx.x == 0) {
+    *(volatile unsigned*)h = *(volatile const unsigned*)d;
+    __threadfence_system();
+  }
+}
 
 af_status map_flags(unsigned f) {
   if (f & FLAG_BOUNDS) return AF_ERR_BOUNDS;
@@ -319,6 +332,13 @@ af_status ensure_staging(af_handle* h) {
 af_status cuda_fail(af_handle* h) {
   if (h) h->broken = 1;
   return AF_ERR_CUDA;
+}
+
+// Enqueues the copy of the device error word into the host mirror (read by the
+// next call without waiting).
+af_status flags_to_host(af_handle* h) {
+  k_flags_to_host<<<1, 32, 0, h->stream>>>(h->d_flags, h->h_flags_dev);
+  return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ERR_CUDA;
 }
 
 // Address under which the current device reaches the host plane p directly:
@@ -636,6 +656,7 @@ af_status af_init(af_handle** out, const af_grid* g, double gamma, const af_stat
   h->red_blocks = 152 * 4;
   bool ok = cudaMalloc(&h->d_flags, sizeof(unsigned)) == cudaSuccess &&
             cudaMallocHost(&h->h_flags, sizeof(unsigned)) == cudaSuccess &&
+            cudaHostGetDevicePointer((void**)&h->h_flags_dev, h->h_flags, 0) == cudaSuccess &&
             cudaMalloc(&h->d_red, sizeof(double) * (RED_VALS * h->red_blocks + AF_NINV)) ==
                 cudaSuccess &&
             cudaMallocHost(&h->h_red, sizeof(double) * AF_NINV) == cudaSuccess;
@@ -701,9 +722,7 @@ af_status af_step(af_handle* h, double dt, int32_t n_steps) {
     h->cur = 1 - h->cur;
   }
   if (cudaGetLastError() != cudaSuccess) return cuda_fail(h);
-  if (cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                      h->stream) != cudaSuccess)
-    return cuda_fail(h);
+  if (flags_to_host(h) != AF_OK) return cuda_fail(h);
   return AF_OK;
 }
 
@@ -712,9 +731,7 @@ af_status af_sync(af_handle* h) {
   if (h->broken) return AF_ERR_STATE;
   DeviceGuard guard(h->device);
   if (wait_outgoing(h) != AF_OK) return AF_ERR_CUDA;
-  if (cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                      h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess)
+  if (flags_to_host(h) != AF_OK || cudaStreamSynchronize(h->stream) != cudaSuccess)
     return cuda_fail(h);
   h->out_pending = 0;
   h->apending[0] = h->apending[1] = 0;
