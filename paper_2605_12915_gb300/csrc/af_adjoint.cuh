@@ -35,7 +35,8 @@ struct AdjView {
                  // 20 + 4 fam (4 values per cell: rho, u, v, p; family 3 is the
                  // centre); increment records of (s, fam) at 36 + 4 (4 s + fam)
                  // (du, dv, dp, 0); half- and full-step points 68 + 4 fam + k and
-                 // 80 + 4 fam + k (planes)
+                 // 80 + 4 fam + k (planes); the centre adjoint lambda_U of each
+                 // cell 92 + k (planes)
   size_t ps;
   int nx, ny;
   T h, dt;
@@ -46,7 +47,8 @@ struct AdjView {
 };
 
 constexpr int LAM_IN = 0, LAM_OUT = 16, LAM_NODE = 20, LAM_INC = 36, LAM_HALF = 68, LAM_FULL = 80;
-constexpr int LAM_PLANES = 92;
+constexpr int LAM_LU = 92;
+constexpr int LAM_PLANES = 96;
 constexpr int SCR_INC = 4, SCR_HALF = 28;
 
 // family of lattice offset (a, b) from a cell's vertex: V, E_v, E_h, C
@@ -595,25 +597,29 @@ __global__ void __launch_bounds__(256, AF_ADJ_NODE_MINB)
 }
 
 // ---------------------------------------------------------------------------
-// Centre recovery (Eq. center-node), reversed.
+// Centre recovery (Eq. center-node), reversed, in two parts: k_adj_center turns
+// each cell's centre adjoint lambda_W into lambda_U (the adjoint of the
+// recovered conserved centre), adds its 9/4 share to the cell average's lambda
+// and stores lambda_U; k_adj_out then gives every vertex and edge node the
+// -1/16 and -1/4 shares of the cells around it (a gather: four cells for a
+// vertex, two for an edge, no atomics) before writing lambda^n out.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256, AF_ADJ_NODE_MINB)
     k_adj_center(const __grid_constant__ AdjView<T> v) {
-  const VecAdj<T> acc = vec_adj(v);
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const size_t ps = v.ps;
   if (i < v.nx && j < v.ny) {
     const size_t id = (size_t)j * v.nx + i;
     T* lc = v.lam + (size_t)(LAM_NODE + 12) * ps + 4 * id;  // the centre node's record
     const T lw[4] = {lc[0], lc[1], lc[2], lc[3]};
+    T lU[4] = {T(0), T(0), T(0), T(0)};
     if (lw[0] != T(0) || lw[1] != T(0) || lw[2] != T(0) || lw[3] != T(0)) {
       zero4(lc);
       const Gas<T>& g = v.gas;
       // the recovered centre (rho~, u, v, p~) is W(U_c); lambda_U = (dW/dU)^T lambda_W
       const T rho = g.rho_ref + v.scr[id], u = v.scr[ps + id], w = v.scr[2 * ps + id];
       const T ri = T(1) / rho;
-      T lU[4];
       lU[0] = lw[0] - u * ri * lw[1] - w * ri * lw[2] + g.gm1 * T(0.5) * (u * u + w * w) * lw[3];
       lU[1] = ri * lw[1] - g.gm1 * u * lw[3];
       lU[2] = ri * lw[2] - g.gm1 * w * lw[3];
@@ -622,17 +628,9 @@ __global__ void __launch_bounds__(256, AF_ADJ_NODE_MINB)
       // average of this cell has no other writer in this kernel
 #pragma unroll
       for (int k = 0; k < 4; ++k) v.lam[(size_t)(LAM_OUT + k) * ps + id] += T(2.25) * lU[k];
-      constexpr int nodes[8][2] = {{0, 0}, {2, 0}, {0, 2}, {2, 2}, {1, 0}, {1, 2}, {0, 1}, {2, 1}};
-#pragma unroll
-      for (int n = 0; n < 8; ++n) {
-        const int fam = fam_of(nodes[n][0], nodes[n][1]);
-        const int cx = i + (nodes[n][0] >> 1), cy = j + (nodes[n][1] >> 1);
-        const Prim<T> wn = node_w(v, fam, cell_id(v, cx, cy));
-        T o[4] = {T(0), T(0), T(0), T(0)};
-        dcons_dprim_T(wn, g, lU, n < 4 ? T(-0.0625) : T(-0.25), o);
-        acc.node(fam, cx, cy, o[0], o[1], o[2], o[3]);
-      }
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v.lam[(size_t)(LAM_LU + k) * ps + id] = lU[k];
   }
 }
 
@@ -977,15 +975,38 @@ struct AdjOut {
 template <typename T>
 __global__ void k_adj_out(const __grid_constant__ AdjView<T> v,
                           const __grid_constant__ AdjOut<T> o, size_t n) {
+  const size_t ps = v.ps;
+  const Gas<T>& g = v.gas;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (size_t)gridDim.x * blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) o.dst[k][t] = (double)v.lam[(size_t)(LAM_OUT + k) * v.ps + t];
+    for (int k = 0; k < 4; ++k) o.dst[k][t] = (double)v.lam[(size_t)(LAM_OUT + k) * ps + t];
+    // lambda_U of the cells around this cell's vertex (i, j): (i, j), (i-1, j),
+    // (i, j-1), (i-1, j-1); the x-edge (i+1/2, j) lies in (i, j) and (i, j-1),
+    // the y-edge (i, j+1/2) in (i, j) and (i-1, j)
+    const int j = (int)(t / (size_t)v.nx), i = (int)(t - (size_t)j * v.nx);
+    const size_t il = (size_t)j * v.nx + wrapc(i - 1, v.nx);
+    const size_t jb = (size_t)wrapc(j - 1, v.ny) * v.nx;
+    const size_t ib = jb + i, ilb = jb + wrapc(i - 1, v.nx);
+    T lc[4], ll[4], lb[4], llb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T* pl = v.lam + (size_t)(LAM_LU + k) * ps;
+      lc[k] = pl[t];
+      ll[k] = pl[il];
+      lb[k] = pl[ib];
+      llb[k] = pl[ilb];
+    }
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      T* rec = v.lam + (size_t)(LAM_NODE + 4 * f) * v.ps + 4 * t;
+      T* rec = v.lam + (size_t)(LAM_NODE + 4 * f) * ps + 4 * t;
+      T r[4] = {rec[0], rec[1], rec[2], rec[3]}, sum[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) o.dst[4 + 4 * f + k][t] = (double)rec[k];
+      for (int k = 0; k < 4; ++k)
+        sum[k] = f == 0 ? (lc[k] + ll[k]) + (lb[k] + llb[k]) : (f == 1 ? lc[k] + ll[k] : lc[k] + lb[k]);
+      dcons_dprim_T(node_w(v, f, t), g, sum, f == 0 ? T(-0.0625) : T(-0.25), r);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) o.dst[4 + 4 * f + k][t] = (double)r[k];
       zero4(rec);
     }
   }
