@@ -492,21 +492,47 @@ struct LoadAdjPUV {
   }
 };
 
-// adds (lp, lu, lv) to the record of the node at lattice offset (dx, dy)
+// adds (lp, lu, lv) to the record of the node at lattice offset (dx, dy).
+// The warp is one row of consecutive nodes (lane = x offset); `act` holds the
+// lanes taking part.  pair() takes a member (dx, dy), dx > 0, and its mirror
+// (-dx, dy): the mirror's target seen from lane k + delta (delta = the cell
+// distance between the two targets) is the member's target seen from lane k,
+// so lane k adds lane k + delta's mirror values to its own and makes one
+// record update for both; a mirror value whose lane k - delta is not taking
+// part is added on its own.
 template <int FAM, typename T>
 struct ScatterAdj {
   T* lam;
   size_t ps;
   Nbhd b;
+  unsigned act;
+  __device__ __forceinline__ T* rec(int ax, int by) const {
+    return lam + (size_t)(LAM_NODE + 4 * fam_of(ax, by)) * ps + 4 * b.at(ax >> 1, by >> 1);
+  }
   __device__ __forceinline__ void operator()(int dx, int dy, T lp, T lu, T lv) const {
-    const int ax = ((FAM == 2 || FAM == 3) ? 1 : 0) + dx, by = ((FAM == 1 || FAM == 3) ? 1 : 0) + dy;
-    T* rec = lam + (size_t)(LAM_NODE + 4 * fam_of(ax, by)) * ps + 4 * b.at(ax >> 1, by >> 1);
-    add4_always(rec, T(0), lu, lv, lp);
+    constexpr int ox = (FAM == 2 || FAM == 3) ? 1 : 0, oy = (FAM == 1 || FAM == 3) ? 1 : 0;
+    add4_always(rec(ox + dx, oy + dy), T(0), lu, lv, lp);
+  }
+  __device__ __forceinline__ void pair(int dx, int dy, T lp, T lu, T lv, T mp, T mu,
+                                       T mv) const {
+    constexpr int ox = (FAM == 2 || FAM == 3) ? 1 : 0, oy = (FAM == 1 || FAM == 3) ? 1 : 0;
+    const int ax = ox + dx, am = ox - dx, by = oy + dy;
+    const int delta = (ax >> 1) - (am >> 1);  // 1 or 2 (compile time once inlined)
+    const int lane = threadIdx.x & 31;
+    const T sp = __shfl_down_sync(act, mp, delta), su = __shfl_down_sync(act, mu, delta),
+            sv = __shfl_down_sync(act, mv, delta);
+    const bool take = lane + delta < 32 && ((act >> (lane + delta)) & 1u);
+    const bool alone = lane < delta || !((act >> (lane - delta)) & 1u);
+    add4_always(rec(ax, by), T(0), take ? lu + su : lu, take ? lv + sv : lv, take ? lp + sp : lp);
+    if (alone) add4_always(rec(am, by), T(0), mu, mv, mp);
   }
 };
 
+// `row`: the lanes of the calling warp (one row of 32 consecutive nodes) inside
+// the grid
 template <int FAM, typename T, typename Acc>
-__device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc, int i, int j) {
+__device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc, int i, int j,
+                                             unsigned row) {
   const size_t ps = v.ps, id = (size_t)j * v.nx + i;
   T ld[2][3];
   bool any = false;
@@ -519,6 +545,8 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
       any = any || ld[s][k] != T(0);
     }
   }
+  // the lanes of the row that have work: they take part in the merged scatter
+  const unsigned act = __ballot_sync(row, any);
   if (!any) return;
 #pragma unroll
   for (int s = 0; s < 2; ++s) zero4(v.lam + (size_t)(LAM_INC + 4 * (4 * s + FAM)) * ps + 4 * id);
@@ -578,7 +606,7 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
   const T lrho = c * lZ - lc * c / (T(2) * rk);
   const T lp = lc * c / (T(2) * pk);
   T lpK = T(0), luK = T(0), lvK = T(0);
-  const ScatterAdj<FAM, T> S = {v.lam, v.ps, nb};
+  const ScatterAdj<FAM, T> S = {v.lam, v.ps, nb, act};
   sac_family_adj<FAM, T>(S, lGp, lGuv, lpK, luK, lvK);
   acc.node(FAM, i, j, lrho, luK, lvK, lp + lpK);
 }
@@ -592,8 +620,10 @@ __device__ __forceinline__ void acoustic_adj(const AdjView<T>& v, const Acc& acc
 template <int FAM, typename T>
 __global__ void __launch_bounds__(256, AF_ADJ_NODE_MINB)
     k_adj_acoustic(const __grid_constant__ AdjView<T> v) {
+  // a warp is one row of 32 consecutive nodes (blockDim.x == 32)
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i < v.nx && j < v.ny) acoustic_adj<FAM>(v, vec_adj(v), i, j);
+  const unsigned row = __ballot_sync(0xffffffffu, i < v.nx && j < v.ny);
+  if (i < v.nx && j < v.ny) acoustic_adj<FAM>(v, vec_adj(v), i, j, row);
 }
 
 // ---------------------------------------------------------------------------

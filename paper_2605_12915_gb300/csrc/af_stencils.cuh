@@ -361,8 +361,8 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
-    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+    S.pair(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev,
+           T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
   }
   {  // orbit (+-1, +-1) half cells
     const T leep = fma(T(1.33333333333333333333), lGp[0][3], fma(T(-4.0), lGp[0][2], fma(T(2.5464790894703253723), lGp[0][1], T(0))));
@@ -377,10 +377,10 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
   {  // orbit (+-1, +-2) half cells
     const T leep = fma(T(-0.666666666666666666667), lGp[0][3], fma(T(1.5), lGp[0][2], fma(T(-0.636619772367581343076), lGp[0][1], T(0))));
@@ -395,10 +395,10 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(1, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(1, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-1, 2, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-1, -2, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(1, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(1, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
   {  // orbit (+-2, +-0) half cells
     const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-2.0), lGp[0][2], fma(T(1.95492965855137201461), lGp[0][1], fma(T(-0.5), lGp[0][0], T(0)))));
@@ -409,8 +409,8 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(2, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
-    S(-2, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+    S.pair(2, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev,
+           T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
   }
   {  // orbit (+-2, +-1) half cells
     const T leep = fma(T(-0.666666666666666666667), lGp[0][3], fma(T(1.5), lGp[0][2], fma(T(-0.636619772367581343076), lGp[0][1], T(0))));
@@ -425,10 +425,10 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-2, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-2, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
   {  // orbit (+-2, +-2) half cells
     const T leep = fma(T(0.333333333333333333333), lGp[0][3], fma(T(-0.5), lGp[0][2], fma(T(0.159154943091895335769), lGp[0][1], T(0))));
@@ -443,10 +443,10 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(2, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(2, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-2, 2, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-2, -2, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(2, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(2, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
 }
 
@@ -638,8 +638,8 @@ __device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
-    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+    S.pair(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev,
+           T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
   }
   {  // orbit (+-1, +-1) half cells
     const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(2.0), lGp[0][2], T(0)));
@@ -654,10 +654,10 @@ __device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
   {  // orbit (+-2, +-0) half cells
     const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(1.0), lGp[0][2], fma(T(1.0), lGp[0][1], fma(T(-0.5), lGp[0][0], T(0)))));
@@ -668,8 +668,8 @@ __device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(2, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
-    S(-2, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+    S.pair(2, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev,
+           T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
   }
   {  // orbit (+-2, +-1) half cells
     const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-0.5), lGp[0][2], T(0)));
@@ -684,10 +684,10 @@ __device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-2, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-2, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
 }
 
@@ -891,8 +891,8 @@ __device__ __forceinline__ void af_sac_EH_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
-    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+    S.pair(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev,
+           T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
   }
   {  // orbit (+-1, +-1) half cells
     const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(2.0), lGp[0][2], T(0)));
@@ -907,10 +907,10 @@ __device__ __forceinline__ void af_sac_EH_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
   {  // orbit (+-1, +-2) half cells
     const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-0.5), lGp[0][2], T(0)));
@@ -925,10 +925,10 @@ __device__ __forceinline__ void af_sac_EH_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(1, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(1, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-1, 2, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-1, -2, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(1, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(1, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
 }
 
@@ -1031,8 +1031,8 @@ __device__ __forceinline__ void af_sac_C_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev);
-    S(-1, 0, T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
+    S.pair(1, 0, T(0) + leep + loep, T(0) + leeu + loeu, T(0) + leev,
+           T(0) + leep - loep, T(0) + leeu - loeu, T(0) + leev);
   }
   {  // orbit (+-1, +-1) half cells
     const T leep = fma(T(1.33333333333333333333), lGp[0][3], T(0));
@@ -1047,9 +1047,9 @@ __device__ __forceinline__ void af_sac_C_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov);
-    S(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov);
-    S(-1, 1, T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S(-1, -1, T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.pair(1, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
+    S.pair(1, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
   }
 }

@@ -240,7 +240,10 @@ def emit_family(name, reps):
 def emit_family_adjoint(name, reps):
     """Transpose of emit_family: given the adjoints lGp, lGuv of the outputs,
     scatter the adjoints of the lattice values through S(dx, dy, lp, lu, lv) and
-    accumulate those of the node's own values (deviation form) into lpK, luK, lvK."""
+    accumulate those of the node's own values (deviation form) into lpK, luK, lvK.
+    A member (dx, dy) with dx > 0 and its mirror (-dx, dy) go out together as
+    S.pair(dx, dy, lp, lu, lv, lp', lu', lv') (the mirror's values second), so that
+    a scatter can merge targets that neighbouring nodes of a row share."""
     lines = []
     lines.append("// family %s, transposed: lattice adjoints from output adjoints" % name)
     lines.append("template <typename T, typename Scatter>")
@@ -275,6 +278,7 @@ def emit_family_adjoint(name, reps):
         for f in CH_IN:
             if (f, (0, 0)) in lam:
                 lines.append("    %s -= T(%d) * %s;" % (kname[f], len(members), lam[(f, (0, 0))]))
+        member_vals = {}
         for (dx, dy) in members:
             sx = 1 if dx >= 0 else -1
             sy = 1 if dy >= 0 else -1
@@ -289,7 +293,15 @@ def emit_family_adjoint(name, reps):
                     expr.append(("+" if sgn > 0 else "-") + " " + nm)
                 e = " ".join(expr) if expr else "+ T(0)"
                 vals.append("T(0) " + e)
-            lines.append("    S(%d, %d, %s, %s, %s);" % (dx, dy, vals[0], vals[1], vals[2]))
+            member_vals[(dx, dy)] = vals
+        for (dx, dy) in members:
+            vals = member_vals[(dx, dy)]
+            if dx > 0 and (-dx, dy) in member_vals:
+                mv = member_vals[(-dx, dy)]
+                lines.append("    S.pair(%d, %d, %s, %s, %s," % (dx, dy, vals[0], vals[1], vals[2]))
+                lines.append("           %s, %s, %s);" % (mv[0], mv[1], mv[2]))
+            elif dx == 0 or (-dx, dy) not in member_vals:
+                lines.append("    S(%d, %d, %s, %s, %s);" % (dx, dy, vals[0], vals[1], vals[2]))
         lines.append("  }")
     lines.append("}")
     lines.append("")

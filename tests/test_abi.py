@@ -190,8 +190,9 @@ def test_generated_tables_match_oracle_operator(orc, fam_name, fam):
 def parse_adjoint(fam_name):
     """The generated transposed stencil af_sac_<fam>_adj as a Python function
     (lGp, lGuv) -> ({(dx, dy): [lp, lu, lv]}, [lpK, luK, lvK]), by evaluating
-    its statements in order."""
-    body, inside = [], False
+    its statements in order (S.pair(dx, dy, member values, mirror values)
+    scatters to (dx, dy) and (-dx, dy))."""
+    body, inside, pending = [], False, ""
     for line in open(STENCILS):
         if line.startswith("__device__ __forceinline__ void af_sac_%s_adj(" % fam_name):
             inside = True
@@ -199,7 +200,12 @@ def parse_adjoint(fam_name):
         if inside:
             if line.startswith("}"):
                 break
-            body.append(line.strip())
+            st = (pending + " " + line.strip()).strip() if pending else line.strip()
+            if st.startswith("S.pair(") and not st.endswith(";"):
+                pending = st  # a statement continued on the next line
+                continue
+            pending = ""
+            body.append(st)
 
     def run(lGp, lGuv):
         env = {"lGp": lGp, "lGuv": lGuv, "fma": lambda a, b, c: a * b + c, "T": float}
@@ -220,6 +226,16 @@ def parse_adjoint(fam_name):
                 acc = out.setdefault((int(m.group(1)), int(m.group(2))), [0.0, 0.0, 0.0])
                 for k in range(3):
                     acc[k] += vals[k]
+                continue
+            m = re.match(r"S\.pair\((\d+), (-?\d+), (.*)\);$", st)
+            if m:
+                vals = eval("(" + m.group(3) + ")", env)
+                dx, dy = int(m.group(1)), int(m.group(2))
+                assert dx > 0 and len(vals) == 6, st
+                for off, part in (((dx, dy), vals[:3]), ((-dx, dy), vals[3:])):
+                    acc = out.setdefault(off, [0.0, 0.0, 0.0])
+                    for k in range(3):
+                        acc[k] += part[k]
                 continue
             assert st in ("", "}") or st.startswith("{") or st.startswith("//"), st
         return out, kk
