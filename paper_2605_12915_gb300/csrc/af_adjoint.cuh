@@ -195,10 +195,10 @@ __device__ __forceinline__ void dcons_dprim_T(const Prim<T>& w, const Gas<T>& g,
 template <int FAM, typename T, typename Scatter>
 __device__ __forceinline__ void sac_family_adj(const Scatter& S, const T lGp[3][4],
                                                const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
-  if (FAM == 0) af_sac_V_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
-  if (FAM == 1) af_sac_EV_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
-  if (FAM == 2) af_sac_EH_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
-  if (FAM == 3) af_sac_C_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+  if constexpr (FAM == 0) af_sac_V_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+  if constexpr (FAM == 1) af_sac_EV_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+  if constexpr (FAM == 2) af_sac_EH_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
+  if constexpr (FAM == 3) af_sac_C_adj<T>(S, lGp, lGuv, lpK, luK, lvK);
 }
 
 
@@ -525,6 +525,38 @@ struct ScatterAdj {
     const bool alone = lane < delta || !((act >> (lane - delta)) & 1u);
     add4_always(rec(ax, by), T(0), take ? lu + su : lu, take ? lv + sv : lv, take ? lp + sp : lp);
     if (alone) add4_always(rec(am, by), T(0), mu, mv, mp);
+  }
+  // members (2, dy), (-2, dy), (0, dy) of a family whose own column is even:
+  // three consecutive nodes of one row, the right one lane k + 1's centre, the
+  // left one lane k - 1's.  Each lane updates its centre with its neighbours'
+  // right and left values, and its own right (left) value alone when lane
+  // k + 1 (k - 1) is not taking part.
+  __device__ __forceinline__ void triple(int dy, T rp, T ru, T rv, T lp, T lu, T lv, T cp, T cu,
+                                         T cv) const {
+    static_assert(FAM == 0 || FAM == 1, "the node's own column is even");
+    constexpr int oy = FAM == 1 ? 1 : 0;
+    const int by = oy + dy;
+    const int lane = threadIdx.x & 31;
+    const T ip = __shfl_up_sync(act, rp, 1), iu = __shfl_up_sync(act, ru, 1),
+            iv = __shfl_up_sync(act, rv, 1);  // lane k - 1's right values
+    const T jp = __shfl_down_sync(act, lp, 1), ju = __shfl_down_sync(act, lu, 1),
+            jv = __shfl_down_sync(act, lv, 1);  // lane k + 1's left values
+    const bool from_l = lane >= 1 && ((act >> (lane - 1)) & 1u);
+    const bool from_r = lane <= 30 && ((act >> (lane + 1)) & 1u);
+    T p = cp, u = cu, w = cv;
+    if (from_l) {
+      p += ip;
+      u += iu;
+      w += iv;
+    }
+    if (from_r) {
+      p += jp;
+      u += ju;
+      w += jv;
+    }
+    add4_always(rec(0, by), T(0), u, w, p);
+    if (!from_r) add4_always(rec(2, by), T(0), ru, rv, rp);
+    if (!from_l) add4_always(rec(-2, by), T(0), lu, lv, lp);
   }
 };
 

@@ -328,6 +328,10 @@ __device__ __forceinline__ void af_sac_V(const Load& L, T pK, T uK, T vK, T Gp[3
 // family V, transposed: lattice adjoints from output adjoints
 template <typename T, typename Scatter>
 __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4], const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
+  T c0m2[3];  // the values of member (0, -2), held for its triple
+  T c0m1[3];  // the values of member (0, -1), held for its triple
+  T c0p1[3];  // the values of member (0, 1), held for its triple
+  T c0p2[3];  // the values of member (0, 2), held for its triple
   {  // orbit (+-0, +-1) half cells
     const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(5.0), lGp[0][2], fma(T(-5.81971863420548805845), lGp[0][1], fma(T(2.0), lGp[0][0], T(0)))));
     const T leop = fma(T(1.0), lGp[2][3], fma(T(-3.87981242280365870564), lGp[2][2], fma(T(5.0), lGp[2][1], fma(T(-2.0), lGp[2][0], T(0)))));
@@ -337,8 +341,12 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(0, 1, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
-    S(0, -1, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+    c0p1[0] = T(0) + leep + leop;
+    c0p1[1] = T(0) + leeu;
+    c0p1[2] = T(0) + leev + leov;
+    c0m1[0] = T(0) + leep - leop;
+    c0m1[1] = T(0) + leeu;
+    c0m1[2] = T(0) + leev - leov;
   }
   {  // orbit (+-0, +-2) half cells
     const T leep = fma(T(0.666666666666666666667), lGp[0][3], fma(T(-2.0), lGp[0][2], fma(T(1.95492965855137201461), lGp[0][1], fma(T(-0.5), lGp[0][0], T(0)))));
@@ -349,8 +357,12 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(0, 2, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
-    S(0, -2, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+    c0p2[0] = T(0) + leep + leop;
+    c0p2[1] = T(0) + leeu;
+    c0p2[2] = T(0) + leev + leov;
+    c0m2[0] = T(0) + leep - leop;
+    c0m2[1] = T(0) + leeu;
+    c0m2[2] = T(0) + leev - leov;
   }
   {  // orbit (+-1, +-0) half cells
     const T leep = fma(T(-1.33333333333333333333), lGp[0][3], fma(T(5.0), lGp[0][2], fma(T(-5.81971863420548805845), lGp[0][1], fma(T(2.0), lGp[0][0], T(0)))));
@@ -425,10 +437,12 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S.pair(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
-           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S.pair(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
-           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.triple(1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+             T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov,
+             c0p1[0], c0p1[1], c0p1[2]);
+    S.triple(-1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+             T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov,
+             c0m1[0], c0m1[1], c0m1[2]);
   }
   {  // orbit (+-2, +-2) half cells
     const T leep = fma(T(0.333333333333333333333), lGp[0][3], fma(T(-0.5), lGp[0][2], fma(T(0.159154943091895335769), lGp[0][1], T(0))));
@@ -443,10 +457,12 @@ __device__ __forceinline__ void af_sac_V_adj(const Scatter& S, const T lGp[3][4]
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S.pair(2, 2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
-           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S.pair(2, -2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
-           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.triple(2, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+             T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov,
+             c0p2[0], c0p2[1], c0p2[2]);
+    S.triple(-2, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+             T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov,
+             c0m2[0], c0m2[1], c0m2[2]);
   }
 }
 
@@ -617,6 +633,8 @@ __device__ __forceinline__ void af_sac_EV(const Load& L, T pK, T uK, T vK, T Gp[
 // family EV, transposed: lattice adjoints from output adjoints
 template <typename T, typename Scatter>
 __device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4], const T lGuv[3][4], T& lpK, T& luK, T& lvK) {
+  T c0m1[3];  // the values of member (0, -1), held for its triple
+  T c0p1[3];  // the values of member (0, 1), held for its triple
   {  // orbit (+-0, +-1) half cells
     const T leep = fma(T(1.33333333333333333333), lGp[0][3], fma(T(-3.0), lGp[0][2], fma(T(2.0), lGp[0][1], T(0))));
     const T leop = fma(T(-0.666666666666666666667), lGp[2][2], fma(T(1.5), lGp[2][1], fma(T(-1.0), lGp[2][0], T(0))));
@@ -626,8 +644,12 @@ __device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(2) * leep;
     luK -= T(2) * leeu;
     lvK -= T(2) * leev;
-    S(0, 1, T(0) + leep + leop, T(0) + leeu, T(0) + leev + leov);
-    S(0, -1, T(0) + leep - leop, T(0) + leeu, T(0) + leev - leov);
+    c0p1[0] = T(0) + leep + leop;
+    c0p1[1] = T(0) + leeu;
+    c0p1[2] = T(0) + leev + leov;
+    c0m1[0] = T(0) + leep - leop;
+    c0m1[1] = T(0) + leeu;
+    c0m1[2] = T(0) + leev - leov;
   }
   {  // orbit (+-1, +-0) half cells
     const T leep = fma(T(2.66666666666666666667), lGp[0][3], fma(T(-4.0), lGp[0][2], fma(T(-2.0), lGp[0][1], fma(T(2.0), lGp[0][0], T(0)))));
@@ -684,10 +706,12 @@ __device__ __forceinline__ void af_sac_EV_adj(const Scatter& S, const T lGp[3][4
     lpK -= T(4) * leep;
     luK -= T(4) * leeu;
     lvK -= T(4) * leev;
-    S.pair(2, 1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
-           T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov);
-    S.pair(2, -1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
-           T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov);
+    S.triple(1, T(0) + leep + loep + leop, T(0) + leeu + loeu + loou, T(0) + leev + leov + loov,
+             T(0) + leep - loep + leop, T(0) + leeu - loeu - loou, T(0) + leev + leov - loov,
+             c0p1[0], c0p1[1], c0p1[2]);
+    S.triple(-1, T(0) + leep + loep - leop, T(0) + leeu + loeu - loou, T(0) + leev - leov - loov,
+             T(0) + leep - loep - leop, T(0) + leeu - loeu + loou, T(0) + leev - leov + loov,
+             c0m1[0], c0m1[1], c0m1[2]);
   }
 }
 

@@ -243,12 +243,28 @@ def emit_family_adjoint(name, reps):
     accumulate those of the node's own values (deviation form) into lpK, luK, lvK.
     A member (dx, dy) with dx > 0 and its mirror (-dx, dy) go out together as
     S.pair(dx, dy, lp, lu, lv, lp', lu', lv') (the mirror's values second), so that
-    a scatter can merge targets that neighbouring nodes of a row share."""
+    a scatter can merge targets that neighbouring nodes of a row share.  Where
+    the node's own column is even (families V and EV), the members (2, dy),
+    (-2, dy) and (0, dy) hit three consecutive nodes of one family and row; they
+    go out together as S.triple(dy, right, left, centre), the values of (0, dy)
+    held from their orbit's block in function-scope temporaries."""
     lines = []
     lines.append("// family %s, transposed: lattice adjoints from output adjoints" % name)
     lines.append("template <typename T, typename Scatter>")
     lines.append("__device__ __forceinline__ void af_sac_%s_adj(const Scatter& S, const T lGp[3][4],"
                  " const T lGuv[3][4], T& lpK, T& luK, T& lvK) {" % name)
+    # rows (dy) whose (0, dy) member joins the (+-2, dy) members in one triple
+    even_col = name in ("V", "EV")
+    triple_dy = set()
+    if even_col:
+        for (a, b) in reps:
+            if a == 2 and (0, b) in reps:
+                triple_dy |= {b, -b}
+    for dy in sorted(triple_dy):
+        lines.append("  T c0%s[3];  // the values of member (0, %d), held for its triple" % (
+            ("m%d" % -dy) if dy < 0 else ("p%d" % dy), dy))
+    def cname(dy):
+        return "c0" + (("m%d" % -dy) if dy < 0 else ("p%d" % dy))
     for (a, b) in sorted(reps):
         chans = reps[(a, b)]
         lines.append("  {  // orbit (+-%d, +-%d) half cells" % (a, b))
@@ -296,6 +312,16 @@ def emit_family_adjoint(name, reps):
             member_vals[(dx, dy)] = vals
         for (dx, dy) in members:
             vals = member_vals[(dx, dy)]
+            if dx == 0 and dy in triple_dy:
+                for k in range(3):
+                    lines.append("    %s[%d] = %s;" % (cname(dy), k, vals[k]))
+                continue
+            if dx == 2 and dy in triple_dy:
+                mv = member_vals[(-dx, dy)]
+                lines.append("    S.triple(%d, %s, %s, %s," % (dy, vals[0], vals[1], vals[2]))
+                lines.append("             %s, %s, %s," % (mv[0], mv[1], mv[2]))
+                lines.append("             %s[0], %s[1], %s[2]);" % (cname(dy), cname(dy), cname(dy)))
+                continue
             if dx > 0 and (-dx, dy) in member_vals:
                 mv = member_vals[(-dx, dy)]
                 lines.append("    S.pair(%d, %d, %s, %s, %s," % (dx, dy, vals[0], vals[1], vals[2]))

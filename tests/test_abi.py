@@ -191,7 +191,8 @@ def parse_adjoint(fam_name):
     """The generated transposed stencil af_sac_<fam>_adj as a Python function
     (lGp, lGuv) -> ({(dx, dy): [lp, lu, lv]}, [lpK, luK, lvK]), by evaluating
     its statements in order (S.pair(dx, dy, member values, mirror values)
-    scatters to (dx, dy) and (-dx, dy))."""
+    scatters to (dx, dy) and (-dx, dy); S.triple(dy, right, left, centre) to
+    (2, dy), (-2, dy) and (0, dy))."""
     body, inside, pending = [], False, ""
     for line in open(STENCILS):
         if line.startswith("__device__ __forceinline__ void af_sac_%s_adj(" % fam_name):
@@ -201,7 +202,7 @@ def parse_adjoint(fam_name):
             if line.startswith("}"):
                 break
             st = (pending + " " + line.strip()).strip() if pending else line.strip()
-            if st.startswith("S.pair(") and not st.endswith(";"):
+            if st.startswith(("S.pair(", "S.triple(")) and not st.endswith(";"):
                 pending = st  # a statement continued on the next line
                 continue
             pending = ""
@@ -215,6 +216,24 @@ def parse_adjoint(fam_name):
             m = re.match(r"const T (\w+) = (.*);$", st)
             if m:
                 env[m.group(1)] = eval(m.group(2), env)
+                continue
+            m = re.match(r"T (c0\w+)\[3\];", st)
+            if m:
+                env[m.group(1)] = [0.0, 0.0, 0.0]
+                continue
+            m = re.match(r"(c0\w+)\[(\d)\] = (.*);$", st)
+            if m:
+                env[m.group(1)][int(m.group(2))] = eval(m.group(3), env)
+                continue
+            m = re.match(r"S\.triple\((-?\d+), (.*)\);$", st)
+            if m:
+                vals = eval("(" + m.group(2) + ")", env)
+                dy = int(m.group(1))
+                assert len(vals) == 9, st
+                for off, part in (((2, dy), vals[:3]), ((-2, dy), vals[3:6]), ((0, dy), vals[6:])):
+                    acc = out.setdefault(off, [0.0, 0.0, 0.0])
+                    for k in range(3):
+                        acc[k] += part[k]
                 continue
             m = re.match(r"(lpK|luK|lvK) -= (.*);$", st)
             if m:
