@@ -54,14 +54,17 @@ def test_one_step_adjoint_dot_product(variant):
 
 
 def test_adjoint_matches_fp64_cpu_adjoint_of_the_oracle(orc):
-    """Transpose of the oracle's one-step Jacobian (central differences, 6x6 grid)."""
+    """Transpose of the oracle's one-step Jacobian (central differences, 6x6
+    grid), applied to a dense random lambda and to sparse ones (unit vectors at
+    seeded entries, and one 2x2 block of cells): with a sparse lambda most nodes
+    of a row have no adjoint to scatter, the case where the scatter's merging of
+    neighbouring nodes' record updates must fall back to single updates."""
     P = I.random_smooth(6, 6, seed=21, amp=0.05, h=1.0 / 6)
     x = P.state
     n = x.size
     eps = 1e-6
     rng = np.random.default_rng(8)
-    lam = rng.normal(size=x.shape)
-    cpu = np.empty(n)
+    jac = np.empty((n, n))  # jac[d] = d y / d x_d
     flat = x.reshape(-1)
     for d in range(n):
         xp = flat.copy()
@@ -70,12 +73,22 @@ def test_adjoint_matches_fp64_cpu_adjoint_of_the_oracle(orc):
         xm[d] -= eps
         yp, _ = orc.step(xp.reshape(x.shape), P.grid.h, P.gamma, P.dt)
         ym, _ = orc.step(xm.reshape(x.shape), P.grid.h, P.gamma, P.dt)
-        cpu[d] = np.sum(lam * (yp - ym)) / (2 * eps)
+        jac[d] = ((yp - ym) / (2 * eps)).reshape(-1)
+    lams = [rng.normal(size=x.shape)]
+    for d in rng.choice(n, size=6, replace=False):
+        e = np.zeros(n)
+        e[d] = 1.0
+        lams.append(e.reshape(x.shape))
+    block = np.zeros(x.shape)
+    block[:, 2:4, 1:3] = rng.normal(size=(16, 2, 2))
+    lams.append(block)
     s = af.Solver(P.grid, P.gamma, x, precision="fp64")
-    gpu = s.adjoint(P.dt, lam).reshape(-1)
+    for k, lam in enumerate(lams):
+        cpu = jac @ lam.reshape(-1)
+        gpu = s.adjoint(P.dt, lam).reshape(-1)
+        err = np.max(np.abs(gpu - cpu)) / np.max(np.abs(cpu))
+        assert err < 1e-7, (k, err)
     s.close()
-    err = np.max(np.abs(gpu - cpu)) / np.max(np.abs(cpu))
-    assert err < 1e-7, err
 
 
 def _rollout_grad(P, n_steps, every, precision):
