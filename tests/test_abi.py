@@ -105,6 +105,8 @@ def test_calls_on_a_null_handle_are_refused(libaf):
     libaf.af_exchange_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int]
     assert libaf.af_exchange_state(None, None, None, 0) == AF_ERR_ARG
+    libaf.af_exchange_state_async.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert libaf.af_exchange_state_async(None, None, None) == AF_ERR_ARG
     libaf.af_destroy.argtypes = [ctypes.c_void_p]
     libaf.af_destroy(None)  # a no-op
 
